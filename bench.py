@@ -1,0 +1,306 @@
+"""Throughput of the loop-hafnian sieve on GB300 (one JSON line on rank 0).
+
+Step = one loop hafnian of the collision-pattern workload (100-mode Haar kernel, 40 photons over 22
+modes with counts 1..4, gamma = 0, complex128): host pairing plan, slot-matrix gather, every sieve
+term on the GPU, double-double reduction. Inputs are resident on the device when the timed region
+starts; the L2 is flushed (256 MiB write) between timed steps, outside the per-step events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one rank per GPU: every rank evaluates its own loop hafnian (independent
+problems, no data-path collective; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "lhaf sieve terms/s (collision-pattern loop hafnian, FP64)"
+UNIT = "terms/s"
+WORKLOAD = ("collision-pattern loop hafnian: 100-mode Haar interferometer, r ~ U[1.0,1.6], gamma = 0, "
+            "40 photons over 22 modes with counts 1..4 (seeded multinomial), complex128, repeated-pair sieve")
+NOMINAL_FP64_GFLOPS = 152 * 4 * 0.5 * 2 * 2.070  # SMs x sub-partitions x FMA lanes/clk x 2 flops x GHz
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm): the oracle as it stands, on a bounded
+# sample of the same workload's sieve terms, spread over the host cores with a spawn pool.
+# ------------------------------------------------------------------------------------------
+
+
+def _oracle_slice(args):
+    seed, start, stop = args
+    sys.path.insert(0, ROOT)
+    from oracle import lhaf_oracle as lo
+    from paper_2108_01622_gb300 import workloads as wl
+
+    p = wl.collision_lhaf_40(seed=seed)
+    t0 = time.perf_counter()
+    terms = lo.repeated_sieve_terms(p.B, p.gamma, p.reps, start, stop)
+    return len(terms), time.perf_counter() - t0
+
+
+class OracleTimer:
+    """The oracle as it stands, timed on slices of the workload's sieve terms over all host cores
+    (one spawn pool, created before any GPU call)."""
+
+    def __init__(self):
+        import multiprocessing as mp
+
+        from oracle import lhaf_oracle as lo
+        from paper_2108_01622_gb300 import workloads as wl
+
+        p = wl.collision_lhaf_40(seed=2)
+        self.total_terms = lo.repeated_term_count(p.reps)
+        self.cores = os.cpu_count() or 1
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:  # one BLAS thread per worker process: `cores` is the number of processes
+            os.environ[k] = "1"
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+        self.pool.map(_oracle_slice, [(2, 0, 64)] * self.cores)  # workers import numpy, warm up
+        n, dt = _oracle_slice((2, 0, 256))
+        self.per_term = dt / max(n, 1)
+        self.cursor = 256
+
+    def sample(self, seconds: float):
+        per_worker = max(64, int(seconds / self.per_term))
+        chunks = []
+        for _ in range(self.cores):
+            if self.cursor + per_worker > self.total_terms:
+                self.cursor = 0
+            chunks.append((2, self.cursor, self.cursor + per_worker))
+            self.cursor += per_worker
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_slice, chunks)
+        wall = time.perf_counter() - t0
+        done = sum(r[0] for r in res)
+        rate = done / wall
+        return {"value": rate, "unit": UNIT, "cores": self.cores, "kind": "oracle",
+                "sample": f"{done} sieve terms (slices of the {self.total_terms}-term unhalved sum of the same "
+                          f"workload), numpy oracle, {self.cores}-process spawn pool, {wall:.1f} s wall",
+                "ms_per_lhaf": self.total_terms / rate * 1e3, "terms_per_lhaf": self.total_terms}
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, index: int, path: str):
+        self.path = path
+        self.proc = None
+        try:
+            self.f = open(path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={CLOCK_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    timer = OracleTimer()
+    per_step = min(10.0, max(0.3, 150.0 / (args.steps + args.warmup)))
+    rates = []
+    base = None
+    for s in range(args.warmup + args.steps):
+        r = timer.sample(per_step)
+        if s >= args.warmup:
+            rates.append(r["value"])
+        base = r
+    timer.close()
+    value = statistics.median(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": base["ms_per_lhaf"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_2108_01622_gb300 as lg
+    from paper_2108_01622_gb300 import workloads as wl
+
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        timer = OracleTimer()  # spawn pool started before the first GPU call
+        cpu_base = timer.sample(15.0)
+        timer.close()
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    p = wl.collision_lhaf_40(seed=2)
+    T, nd, h, P = lg.plan(p.reps, has_loops=False)
+    ctx = lg.Context(local_rank, stream=torch.cuda.current_stream(dev).cuda_stream)
+    Bd = torch.from_numpy(p.B).to(dev)
+    gd = torch.from_numpy(p.gamma).to(dev)
+    flags = lg.NO_LOOPS
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    fp64_gflops = lg.fp64_probe(local_rank)
+
+    out = torch.empty(1, dtype=torch.complex128, device=dev)
+    for _ in range(args.warmup):
+        ctx.lhaf(Bd, gd, p.reps, flags=flags, out=out)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kern_ms = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+                           if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv")
+    time.sleep(0.3)
+    stats = None
+    for s in range(args.steps):
+        flush.zero_()
+        starts[s].record()
+        _, stats = ctx.lhaf(Bd, gd, p.reps, flags=flags, out=out, stats=True)
+        ends[s].record()
+        kern_ms.append(stats["kernel_ms"])
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps * T / (total_ms * 1e-3)
+    val = complex(out.cpu()[0])
+
+    # e2e: the public host-pointer call (pinned staging copies inside the library) per step
+    e2e_times = []
+    for s in range(max(3, args.steps // 4)):
+        t0 = time.perf_counter()
+        ctx.lhaf(p.B, p.gamma, p.reps)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_ms = statistics.median(e2e_times) * 1e3
+
+    avg_kernel_ms = statistics.mean(kern_ms)
+    flops = stats["flops_model"]
+    achieved = flops / (avg_kernel_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "terms_per_lhaf": T, "n_dim": nd, "h": h, "pairs": P,
+                   "team": stats["team"], "l2": "flushed between steps (256 MiB write, outside step events)",
+                   "parallelism": f"{world} independent loop hafnians, one per GPU"},
+        "ms_per_lhaf": total_ms / args.steps,
+        "gpu_launches": 3 * args.steps,
+        "roofline": {"bound": "alu", "kernel": "terms_kernel (FP64 sieve terms)",
+                     "achieved": achieved, "peak": NOMINAL_FP64_GFLOPS / 1e3, "unit": "TFLOP/s",
+                     "frac": achieved / (NOMINAL_FP64_GFLOPS / 1e3), "traffic": None,
+                     "peak_source": "derived: 152 SMs x 4 sub-partitions x 0.5 FP64 FMA lanes/clk x 2 x 2.070 GHz",
+                     "fp64_probe_tflops": fp64_gflops / 1e3,
+                     "frac_of_probe": achieved / (fp64_gflops / 1e3),
+                     "flops_per_launch": flops, "avg_launch_ms": avg_kernel_ms},
+        "e2e": {"value": T / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_lhaf": e2e_ms,
+                "h2d_bytes_per_step": nd * nd * 16, "d2h_bytes_per_step": 48},
+        "clocks": clocks,
+        "result": [val.real, val.imag],
+    }
+    if cpu_base is not None:
+        line["cpu_baseline"] = {k: cpu_base[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"]["ms_per_lhaf"] = cpu_base["ms_per_lhaf"]
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local_rank = rank_info()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

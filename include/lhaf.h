@@ -1,0 +1,135 @@
+/*
+ * lhaf.h -- C ABI of the GB300 loop-hafnian library (arXiv:2108.01622, "The Boundary for Quantum
+ * Advantage in Gaussian Boson Sampling").
+ *
+ * The library evaluates the loop hafnian lhaf(B_n) of the N x N matrix B_n that is formed from a
+ * complex symmetric M x M matrix B by repeating row/column i reps[i] times and putting the
+ * repeated loop weights gamma on the diagonal (App. A, Eq. mixed_prob and the chain-rule variant
+ * of App. A.2). It uses the finite difference sieve (App. B.4, Eq. fdsieve) over greedily matched
+ * repeated pairs (App. B.2-B.3): prod_i (eta_i + 1) terms, halved by the sign symmetry of the
+ * sieve. Every term runs on the GPU (FP64 by default); the signed sum is accumulated in
+ * double-double.
+ *
+ * Conventions shared by all calls
+ *   - Complex numbers are lhaf_c128 {re, im}: the layout of C99 double _Complex,
+ *     std::complex<double> and torch.complex128.
+ *   - B is M x M, row-major, symmetric; only entries with i <= j are read. B[m][m] is the weight of
+ *     a pair of two photons in mode m; loops come from gamma.
+ *   - gamma has M entries; NULL means gamma[m] = B[m][m] (the loop weights of the repeated matrix
+ *     without diagonal replacement).
+ *   - reps has M non-negative counts and is ALWAYS a host pointer (the host plans the pairing).
+ *     reps == NULL means one photon in every mode. reps[i] = 0 drops mode i. N = sum(reps) may be 0
+ *     (lhaf = 1) or odd (a pad index with loop weight 1 is added, App. B readings).
+ *   - Host-pointer calls (flags without LHAF_DEVICE_PTRS) are synchronous: inputs are copied to the
+ *     device, the result is copied back before the call returns.
+ *   - With LHAF_DEVICE_PTRS, B, gamma and the outputs are device pointers on the context's
+ *     device; the call is ordered on the context's stream and returns without synchronising.
+ *   - Ownership: the caller owns every buffer; the library keeps no pointer after a call returns.
+ *   - Errors are returned as lhaf_status codes; the library never exits or traps.
+ */
+#ifndef LHAF_GB300_H
+#define LHAF_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  double re;
+  double im;
+} lhaf_c128;
+
+typedef enum {
+  LHAF_OK = 0,
+  LHAF_EINVAL = 1,     /* bad argument: NULL required pointer, M <= 0, negative reps, non-finite */
+  LHAF_ETOOBIG = 2,    /* working dimension above LHAF_MAX_DIM, degree above LHAF_MAX_DEGREE,
+                          or more than 2^62 terms */
+  LHAF_ECUDA = 3,      /* a CUDA runtime call failed (no device, launch error, ...) */
+  LHAF_ETIMEOUT = 4,   /* reserved for device watchdogs */
+  LHAF_ENOMEM = 5,     /* device or pinned-host allocation failed */
+  LHAF_ECANCELLED = 6  /* reserved */
+} lhaf_status;
+
+/* Flags (bitwise OR). */
+#define LHAF_DEVICE_PTRS 0x1u        /* B, gamma and outputs are device pointers, stream-ordered */
+#define LHAF_FP32_TERMS 0x2u         /* per-term arithmetic in FP32 (accumulation stays in
+                                        double-double); error is larger, see the tests */
+#define LHAF_PLAIN_ACCUM 0x4u        /* accumulate the signed sum in plain FP64 instead of
+                                        double-double (for accuracy comparisons) */
+#define LHAF_NO_REPEAT_SPEEDUP 0x8u  /* pair photons one by one (all eta = 1): the sieve of the
+                                        explicit duplicated-row matrix, 2^(N/2) terms */
+#define LHAF_NO_LOOPS 0x10u          /* declare gamma == 0 on the occupied modes (skips the loop
+                                        border); with host pointers this is detected by itself */
+
+/* Compiled limits. */
+#define LHAF_MAX_DIM 64      /* working dimension n_dim = 2 * pairs (+1 loop border) */
+#define LHAF_MAX_DEGREE 256  /* h = ceil(N/2) */
+
+typedef struct lhaf_ctx lhaf_ctx;
+
+/* Per-call statistics (optional out-parameter). */
+typedef struct {
+  uint64_t terms;       /* sieve terms evaluated (after the sign-symmetry halving) */
+  int32_t n_dim;        /* working matrix dimension: 2 * pairs, +1 when loops are present */
+  int32_t h;            /* polynomial degree ceil(N/2) */
+  int32_t pairs;        /* unique pairs after greedy matching (+1 pad pair when N is odd) */
+  int32_t team;         /* GPU lanes that share one term */
+  double kernel_ms;     /* device time of the term and reduction kernels (CUDA events) */
+  double flops_model;   /* algorithmic real flops of this call: per term, the complex
+                           multiply-adds of the elimination Hessenberg reduction, La Budde's
+                           recurrence and the series, 8 flops each (lhaf_flops_per_term) */
+} lhaf_stats;
+
+/* Create a context on `device`. cuda_stream: a cudaStream_t to order work on, or NULL for a
+ * stream the context creates and owns. Allocates the context's device workspace.
+ * Returns LHAF_ECUDA if the device cannot be used, LHAF_ENOMEM on allocation failure. */
+lhaf_status lhaf_ctx_create(lhaf_ctx** ctx, int device, void* cuda_stream);
+
+/* Release the context and its workspace (synchronises its stream first). NULL is a no-op. */
+void lhaf_ctx_destroy(lhaf_ctx* ctx);
+
+/* Static description of a status code. */
+const char* lhaf_strerror(lhaf_status status);
+
+/* Plan only (host, no GPU): the greedy pairing of App. B.3 for `reps`, returning the number of
+ * sieve terms after halving, the working dimension and the degree. `has_loops` != 0 counts the
+ * loop border. Any output pointer may be NULL. */
+lhaf_status lhaf_plan(int M, const int32_t* reps, uint32_t flags, int has_loops, uint64_t* terms,
+                      int32_t* n_dim, int32_t* h, int32_t* pairs);
+
+/* lhaf(B_n) (App. B.4 Eq. fdsieve with the repeated pairs of App. B.2-B.4).
+ * out: one lhaf_c128 (host, or device with LHAF_DEVICE_PTRS). stats: host pointer or NULL. */
+lhaf_status lhaf(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128* gamma,
+                 const int32_t* reps, uint32_t flags, lhaf_c128* out, lhaf_stats* stats);
+
+/* Partial sieve sum over the evaluated-term index range [term_begin, term_end) (terms numbered
+ * 0 .. terms-1 as reported by lhaf_plan). partial_dd receives 4 doubles (re_hi, re_lo, im_hi,
+ * im_lo) of the UNSCALED double-double partial sum (host, or device with LHAF_DEVICE_PTRS).
+ * Partials over disjoint ranges add; lhaf = 2^-h * (sum of partials over [0, terms)), see
+ * lhaf_combine. This is the unit for sharding across GPUs and for checkpoint/resume. */
+lhaf_status lhaf_range(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128* gamma,
+                       const int32_t* reps, uint32_t flags, uint64_t term_begin,
+                       uint64_t term_end, double* partial_dd, lhaf_stats* stats);
+
+/* Algorithmic real flops of one sieve term of this implementation for working dimension n_dim,
+ * degree h and loop border flag `bordered` (8 per complex multiply-add of the elimination
+ * Hessenberg reduction, La Budde's recurrence and the series recurrences). 0 for invalid sizes. */
+double lhaf_flops_per_term(int n_dim, int h, int bordered);
+
+/* Host-side double-double sum of `count` partials (4 doubles each, as from lhaf_range) scaled
+ * by 2^-h (exact). */
+lhaf_status lhaf_combine(int count, const double* partials_dd, int32_t h, lhaf_c128* out);
+
+/* Measurement utility (no counterpart in the paper): FP64 fused multiply-add throughput of
+ * `device` in GFLOP/s (2 flops per FMA), from independent FMA chains over every SM for a few tens
+ * of milliseconds. The sieve kernels are bound by this rate; it is the roofline denominator. */
+lhaf_status lhaf_fp64_probe(int device, double* gflops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LHAF_GB300_H */

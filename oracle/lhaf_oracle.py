@@ -301,6 +301,34 @@ def reduced_slot_problem(B, gamma, reps):
     return C, v, etas, h
 
 
+def repeated_sieve_terms(B, gamma, reps, start: int = 0, stop: Optional[int] = None,
+                         batch: int = 2048) -> List[complex]:
+    """The signed, weighted sieve terms prod_i C(eta_i,k_i) (-1)^(k_i) f(C X_delta') for the digit
+    vectors k number start..stop-1 in itertools.product order (App. B.2, B.4). Used by
+    lhaf_repeated (all terms) and by timing on a bounded sample of terms."""
+    C, v, etas, h = reduced_slot_problem(B, gamma, reps)
+    total = math.prod(e + 1 for e in etas)
+    stop = total if stop is None else min(stop, total)
+    digit_ranges = [range(e + 1) for e in etas]
+    all_k = np.array(list(itertools.islice(itertools.product(*digit_ranges), start, stop)), dtype=np.int64)
+    etas_a = np.array(etas, dtype=np.int64)
+    terms: List[complex] = []
+    for b0 in range(0, len(all_k), batch):
+        ks = all_k[b0 : b0 + batch]
+        deltas = (etas_a[None, :] - 2 * ks).astype(float)
+        weights = np.array(
+            [
+                math.prod(math.comb(int(e), int(k)) * (-1) ** int(k) for e, k in zip(etas, row))
+                for row in ks
+            ],
+            dtype=float,
+        )
+        g = _g_coefficients(C, v, _pairing_matrices(deltas), h)
+        f = et_poly_coefficient(g, h)
+        terms.extend((weights * f).tolist())
+    return terms
+
+
 def lhaf_repeated(B, gamma, reps, batch: int = 2048) -> complex:
     """lhaf(A_n) by the finite difference sieve over greedy repeated pairs (App. B.2, B.4).
 
@@ -313,25 +341,8 @@ def lhaf_repeated(B, gamma, reps, batch: int = 2048) -> complex:
     N = int(sum(int(r) for r in reps))
     if N == 0:
         return 1.0 + 0j
-    C, v, etas, h = reduced_slot_problem(B, gamma, reps)
-    digit_ranges = [range(e + 1) for e in etas]
-    all_k = np.array(list(itertools.product(*digit_ranges)), dtype=np.int64)
-    etas_a = np.array(etas, dtype=np.int64)
-    terms = []
-    for start in range(0, len(all_k), batch):
-        ks = all_k[start : start + batch]
-        deltas = (etas_a[None, :] - 2 * ks).astype(float)
-        weights = np.array(
-            [
-                math.prod(math.comb(int(e), int(k)) * (-1) ** int(k) for e, k in zip(etas, row))
-                for row in ks
-            ],
-            dtype=float,
-        )
-        g = _g_coefficients(C, v, _pairing_matrices(deltas), h)
-        f = et_poly_coefficient(g, h)
-        terms.extend((weights * f).tolist())
-    return _fsum_complex(terms) / 2.0**h
+    h = (N + 1) // 2
+    return _fsum_complex(repeated_sieve_terms(B, gamma, reps, batch=batch)) / 2.0**h
 
 
 # ---------------------------------------------------------------------------------------------

@@ -1,0 +1,236 @@
+"""GB300 loop-hafnian library (arXiv:2108.01622): thin Python binding of include/lhaf.h.
+
+Argument marshalling only: every step of the computation runs in the CUDA library
+``liblhaf_gb300.so`` built in-tree by ``paper_2108_01622_gb300.build``. There is no CPU fallback;
+if the library is missing, every call raises ImportError.
+
+Inputs may be numpy arrays (host pointers: synchronous calls) or torch CUDA tensors (device
+pointers: calls ordered on the context's stream, which defaults to torch's current stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblhaf_gb300.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "lhaf.h")
+
+DEVICE_PTRS = 0x1
+FP32_TERMS = 0x2
+PLAIN_ACCUM = 0x4
+NO_REPEAT_SPEEDUP = 0x8
+NO_LOOPS = 0x10
+
+STATUS = {0: "LHAF_OK", 1: "LHAF_EINVAL", 2: "LHAF_ETOOBIG", 3: "LHAF_ECUDA", 4: "LHAF_ETIMEOUT",
+          5: "LHAF_ENOMEM", 6: "LHAF_ECANCELLED"}
+
+
+class LhafError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({_lib().lhaf_strerror(status).decode()})")
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("terms", ctypes.c_uint64), ("n_dim", ctypes.c_int32), ("h", ctypes.c_int32),
+                ("pairs", ctypes.c_int32), ("team", ctypes.c_int32), ("kernel_ms", ctypes.c_double),
+                ("flops_model", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CUDA library not built: {LIB_PATH} (run paper_2108_01622_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, c = ctypes.c_void_p, ctypes
+        L.lhaf_ctx_create.argtypes = [ctypes.POINTER(vp), c.c_int, vp]
+        L.lhaf_ctx_create.restype = c.c_int
+        L.lhaf_ctx_destroy.argtypes = [vp]
+        L.lhaf_ctx_destroy.restype = None
+        L.lhaf_strerror.argtypes = [c.c_int]
+        L.lhaf_strerror.restype = c.c_char_p
+        L.lhaf_plan.argtypes = [c.c_int, vp, c.c_uint32, c.c_int, ctypes.POINTER(c.c_uint64),
+                                ctypes.POINTER(c.c_int32), ctypes.POINTER(c.c_int32), ctypes.POINTER(c.c_int32)]
+        L.lhaf_plan.restype = c.c_int
+        L.lhaf.argtypes = [vp, c.c_int, vp, vp, vp, c.c_uint32, vp, ctypes.POINTER(Stats)]
+        L.lhaf.restype = c.c_int
+        L.lhaf_range.argtypes = [vp, c.c_int, vp, vp, vp, c.c_uint32, c.c_uint64, c.c_uint64, vp,
+                                 ctypes.POINTER(Stats)]
+        L.lhaf_range.restype = c.c_int
+        L.lhaf_combine.argtypes = [c.c_int, vp, c.c_int32, vp]
+        L.lhaf_combine.restype = c.c_int
+        L.lhaf_flops_per_term.argtypes = [c.c_int, c.c_int, c.c_int]
+        L.lhaf_flops_per_term.restype = c.c_double
+        L.lhaf_fp64_probe.argtypes = [c.c_int, ctypes.POINTER(c.c_double)]
+        L.lhaf_fp64_probe.restype = c.c_int
+        _LIB = L
+    return _LIB
+
+
+def header_functions() -> list:
+    """Names of the functions include/lhaf.h declares."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(",
+                                 src, flags=re.M)))
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise LhafError(st, where)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _host_c128(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+
+
+def _reps_arr(reps, M) -> Optional[np.ndarray]:
+    if reps is None:
+        return None
+    r = np.ascontiguousarray(np.asarray(reps, dtype=np.int32))
+    if r.shape != (M,):
+        raise ValueError(f"reps must have shape ({M},)")
+    return r
+
+
+def _ptr(a) -> Optional[int]:
+    if a is None:
+        return None
+    if _is_torch(a):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def plan(reps: Sequence[int], flags: int = 0, has_loops: bool = True) -> Tuple[int, int, int, int]:
+    """(terms, n_dim, h, pairs) of the greedy repeated-pair sieve (App. B.3), host only."""
+    r = np.ascontiguousarray(np.asarray(reps, dtype=np.int32))
+    T, nd, h, P = ctypes.c_uint64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib().lhaf_plan(len(r), r.ctypes.data, flags, int(has_loops), ctypes.byref(T), ctypes.byref(nd),
+                            ctypes.byref(h), ctypes.byref(P)), "lhaf_plan")
+    return T.value, nd.value, h.value, P.value
+
+
+def flops_per_term(n_dim: int, h: int, bordered: bool) -> float:
+    return _lib().lhaf_flops_per_term(n_dim, h, int(bordered))
+
+
+def fp64_probe(device: int = 0) -> float:
+    """Measured FP64 FMA throughput of the device in GFLOP/s."""
+    g = ctypes.c_double()
+    _check(_lib().lhaf_fp64_probe(device, ctypes.byref(g)), "lhaf_fp64_probe")
+    return g.value
+
+
+def combine(partials, h: int) -> complex:
+    p = np.ascontiguousarray(np.asarray(partials, dtype=np.float64).reshape(-1, 4))
+    out = np.zeros(1, np.complex128)
+    _check(_lib().lhaf_combine(p.shape[0], p.ctypes.data, h, out.ctypes.data), "lhaf_combine")
+    return complex(out[0])
+
+
+class Context:
+    """A device context: stream, workspace and the lhaf entry points."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._lib = _lib()
+        self.device = device
+        if stream is None:
+            try:
+                import torch
+
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream(device).cuda_stream
+            except ImportError:
+                pass
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(self._lib.lhaf_ctx_create(ctypes.byref(h), device, stream), "lhaf_ctx_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lhaf_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _inputs(self, B, gamma, reps, flags):
+        dev = _is_torch(B) and B.is_cuda
+        if dev:
+            import torch
+
+            if B.dtype != torch.complex128:
+                raise TypeError("B must be complex128")
+            B = B.contiguous()
+            if gamma is not None:
+                gamma = gamma.to(torch.complex128).contiguous()
+            flags |= DEVICE_PTRS
+        else:
+            B = _host_c128(B)
+            gamma = None if gamma is None else _host_c128(gamma)
+        M = B.shape[0]
+        if tuple(B.shape) != (M, M):
+            raise ValueError("B must be square")
+        if gamma is not None and tuple(gamma.shape) != (M,):
+            raise ValueError("gamma must have shape (M,)")
+        return B, gamma, _reps_arr(reps, M), M, flags
+
+    def lhaf(self, B, gamma=None, reps=None, flags: int = 0, stats: bool = False, out=None):
+        """lhaf(B_n). Host inputs return a Python complex. Device (torch CUDA) inputs write into
+        `out` (a complex128 CUDA tensor of one element, allocated if None) and return it."""
+        B, gamma, r, M, flags = self._inputs(B, gamma, reps, flags)
+        st = Stats()
+        if flags & DEVICE_PTRS:
+            import torch
+
+            if out is None:
+                out = torch.empty(1, dtype=torch.complex128, device=B.device)
+            _check(self._lib.lhaf(self._h, M, _ptr(B), _ptr(gamma), _ptr(r), flags, out.data_ptr(),
+                                  ctypes.byref(st) if stats else None), "lhaf")
+            return (out, st.as_dict()) if stats else out
+        res = np.zeros(1, np.complex128)
+        _check(self._lib.lhaf(self._h, M, _ptr(B), _ptr(gamma), _ptr(r), flags, res.ctypes.data,
+                              ctypes.byref(st) if stats else None), "lhaf")
+        return (complex(res[0]), st.as_dict()) if stats else complex(res[0])
+
+    def lhaf_range(self, B, gamma, reps, term_begin: int, term_end: int, flags: int = 0, stats: bool = False):
+        """Unscaled double-double partial (4 doubles) of the sieve over [term_begin, term_end)."""
+        B, gamma, r, M, flags = self._inputs(B, gamma, reps, flags)
+        st = Stats()
+        if flags & DEVICE_PTRS:
+            import torch
+
+            part = torch.zeros(4, dtype=torch.float64, device=B.device)
+            _check(self._lib.lhaf_range(self._h, M, _ptr(B), _ptr(gamma), _ptr(r), flags, term_begin, term_end,
+                                        part.data_ptr(), ctypes.byref(st) if stats else None), "lhaf_range")
+        else:
+            part = np.zeros(4, np.float64)
+            _check(self._lib.lhaf_range(self._h, M, _ptr(B), _ptr(gamma), _ptr(r), flags, term_begin, term_end,
+                                        part.ctypes.data, ctypes.byref(st) if stats else None), "lhaf_range")
+        return (part, st.as_dict()) if stats else part

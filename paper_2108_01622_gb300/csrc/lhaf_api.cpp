@@ -1,0 +1,375 @@
+// Host side of the loop-hafnian library: pairing planner (App. B.3), slot matrix, term-space
+// partition, team-size choice, workspace and the C ABI of include/lhaf.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/lhaf.h"
+#include "lhaf_internal.h"
+#include "lhaf_plan.h"
+
+using namespace lhafgpu;
+
+struct lhaf_ctx {
+  int device = 0;
+  int sms = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  // device workspace
+  double2* d_chat = nullptr;
+  float2* d_chat32 = nullptr;
+  double* d_partials = nullptr;
+  size_t partial_cap = 0;  // teams
+  double* d_out = nullptr;  // 4 dd doubles + 2 value doubles
+  // pinned host staging
+  double2* h_chat = nullptr;
+  float2* h_chat32 = nullptr;
+  double* h_out = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::mutex mu;
+};
+
+extern "C" const char* lhaf_strerror(lhaf_status s) {
+  switch (s) {
+    case LHAF_OK: return "ok";
+    case LHAF_EINVAL: return "invalid argument";
+    case LHAF_ETOOBIG: return "problem exceeds compiled limits (dimension, degree or term count)";
+    case LHAF_ECUDA: return "CUDA runtime error";
+    case LHAF_ETIMEOUT: return "device watchdog expired";
+    case LHAF_ENOMEM: return "out of memory";
+    case LHAF_ECANCELLED: return "cancelled";
+  }
+  return "unknown status";
+}
+
+extern "C" void lhaf_ctx_destroy(lhaf_ctx* ctx) {
+  if (!ctx) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  cudaFree(ctx->d_chat);
+  cudaFree(ctx->d_chat32);
+  cudaFree(ctx->d_partials);
+  cudaFree(ctx->d_out);
+  cudaFreeHost(ctx->h_chat);
+  cudaFreeHost(ctx->h_chat32);
+  cudaFreeHost(ctx->h_out);
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  cudaSetDevice(prev);
+  delete ctx;
+}
+
+extern "C" lhaf_status lhaf_ctx_create(lhaf_ctx** out, int device, void* cuda_stream) {
+  if (!out) return LHAF_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return LHAF_ECUDA;
+  lhaf_ctx* c = new (std::nothrow) lhaf_ctx();
+  if (!c) return LHAF_ENOMEM;
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete c;
+    return LHAF_ECUDA;
+  }
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return LHAF_ECUDA;
+    }
+    c->own_stream = true;
+  }
+  c->partial_cap = (size_t)c->sms * 32 * 16;  // max CTAs/SM x max teams/CTA
+  const size_t nchat = (size_t)kMaxDim * kMaxDim;
+  bool ok = cudaMalloc(&c->d_chat, nchat * sizeof(double2)) == cudaSuccess &&
+            cudaMalloc(&c->d_chat32, nchat * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc(&c->d_partials, c->partial_cap * 4 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_out, 8 * sizeof(double)) == cudaSuccess &&
+            cudaMallocHost(&c->h_chat, nchat * sizeof(double2)) == cudaSuccess &&
+            cudaMallocHost(&c->h_chat32, nchat * sizeof(float2)) == cudaSuccess &&
+            cudaMallocHost(&c->h_out, 8 * sizeof(double)) == cudaSuccess &&
+            cudaEventCreate(&c->ev0) == cudaSuccess && cudaEventCreate(&c->ev1) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    lhaf_ctx_destroy(c);
+    return LHAF_ENOMEM;
+  }
+  *out = c;
+  return LHAF_OK;
+}
+
+extern "C" lhaf_status lhaf_plan(int M, const int32_t* reps, uint32_t flags, int has_loops, uint64_t* terms,
+                                 int32_t* n_dim, int32_t* h, int32_t* pairs) {
+  Plan pl;
+  lhaf_status st = build_plan(M, reps, flags, has_loops != 0, pl);
+  if (st != LHAF_OK) return st;
+  if (terms) *terms = pl.T;
+  if (n_dim) *n_dim = pl.nd;
+  if (h) *h = pl.h;
+  if (pairs) *pairs = pl.P;
+  return LHAF_OK;
+}
+
+extern "C" lhaf_status lhaf_combine(int count, const double* p, int32_t h, lhaf_c128* out) {
+  if (count < 0 || (count > 0 && !p) || !out || h < 0) return LHAF_EINVAL;
+  double rh = 0, rl = 0, ih = 0, il = 0;
+  for (int i = 0; i < count; i++) {
+    dd_add_dd_host(rh, rl, p[4 * i + 0], p[4 * i + 1]);
+    dd_add_dd_host(ih, il, p[4 * i + 2], p[4 * i + 3]);
+  }
+  out->re = std::ldexp(rh + rl, -h);
+  out->im = std::ldexp(ih + il, -h);
+  return LHAF_OK;
+}
+
+namespace {
+
+bool finite_c(const lhaf_c128& z) { return std::isfinite(z.re) && std::isfinite(z.im); }
+
+// Choose the lanes-per-term team size: a model of FP64 lane utilisation times the share of the
+// four SM sub-partitions that hold at least one warp. LHAF_TEAM in the environment overrides.
+int choose_team(lhaf_ctx* ctx, bool fp32, const Plan& pl, int* ctas_per_sm) {
+  const char* env = std::getenv("LHAF_TEAM");
+  int forced = env ? std::atoi(env) : 0;
+  const int cands[5] = {8, 16, 32, 64, 128};
+  double best = -1.0;
+  int best_g = 32, best_occ = 0;
+  for (int g : cands) {
+    if (forced && g != forced) continue;
+    const size_t smem = cta_shared_bytes(fp32, g, pl.nd, pl.H, pl.Hl, pl.P);
+    if (smem > 227 * 1024) continue;
+    const int occ = max_ctas_per_sm(fp32, g, smem);
+    if (occ <= 0) continue;
+    const double warps = (double)occ * cta_threads(g) / 32.0;
+    const double cover = std::min(1.0, warps / 4.0);
+    const double eff = model_lane_efficiency(pl.nd, pl.Hl, pl.h, pl.bord, g);
+    const double score = eff * cover * (warps >= 8.0 ? 1.0 : 0.9);
+    if (score > best) {
+      best = score;
+      best_g = g;
+      best_occ = occ;
+    }
+  }
+  if (best < 0) return 0;
+  (void)ctx;
+  *ctas_per_sm = best_occ;
+  return best_g;
+}
+
+// Build the slot matrix into ctx->d_chat (and d_chat32 for FP32 terms).
+lhaf_status stage_chat(lhaf_ctx* ctx, const Plan& pl, int M, const lhaf_c128* B, const lhaf_c128* gamma,
+                       uint32_t flags, bool fp32) {
+  const int nd = pl.nd;
+  if (flags & LHAF_DEVICE_PTRS) {
+    cudaError_t e = launch_gather((const double2*)B, (const double2*)gamma, M, pl.slot_mode.data(), pl.P, pl.bord,
+                                  ctx->d_chat, fp32 ? ctx->d_chat32 : nullptr, ctx->stream);
+    return e == cudaSuccess ? LHAF_OK : LHAF_ECUDA;
+  }
+  build_chat_host(pl, M, B, gamma, (std::complex<double>*)ctx->h_chat);
+  cudaError_t e;
+  if (fp32) {
+    for (int i = 0; i < nd * nd; i++) ctx->h_chat32[i] = make_float2((float)ctx->h_chat[i].x, (float)ctx->h_chat[i].y);
+    e = cudaMemcpyAsync(ctx->d_chat32, ctx->h_chat32, (size_t)nd * nd * sizeof(float2), cudaMemcpyHostToDevice,
+                        ctx->stream);
+  } else {
+    e = cudaMemcpyAsync(ctx->d_chat, ctx->h_chat, (size_t)nd * nd * sizeof(double2), cudaMemcpyHostToDevice,
+                        ctx->stream);
+  }
+  return e == cudaSuccess ? LHAF_OK : LHAF_ECUDA;
+}
+
+bool has_loops_host(const Plan& pl, int M, const lhaf_c128* B, const lhaf_c128* gamma) {
+  for (int s = 0; s < 2 * pl.P; s++) {
+    const int m = pl.slot_mode[s];
+    if (m < 0) return true;
+    const lhaf_c128 g = gamma ? gamma[m] : B[(size_t)m * M + m];
+    if (g.re != 0.0 || g.im != 0.0) return true;
+  }
+  return false;
+}
+
+lhaf_status validate_host_inputs(int M, const lhaf_c128* B, const lhaf_c128* gamma, const int32_t* reps) {
+  for (int i = 0; i < M; i++) {
+    const int r = reps ? reps[i] : 1;
+    if (r < 0) return LHAF_EINVAL;
+    if (r == 0) continue;
+    for (int j = 0; j < M; j++) {
+      const int r2 = reps ? reps[j] : 1;
+      if (r2 == 0) continue;
+      const int lo = std::min(i, j), hi = std::max(i, j);
+      if (!finite_c(B[(size_t)lo * M + hi])) return LHAF_EINVAL;
+    }
+    if (gamma && !finite_c(gamma[i])) return LHAF_EINVAL;
+  }
+  return LHAF_OK;
+}
+
+// Runs the sieve over [tb, te) of the plan; writes the dd partial (unscaled) and/or the scaled
+// value into device buffers dd_dst / val_dst.
+lhaf_status run_terms(lhaf_ctx* ctx, const Plan& pl, uint32_t flags, uint64_t tb, uint64_t te, double* dd_dst,
+                      double2* val_dst, lhaf_stats* stats, bool timed) {
+  const bool fp32 = (flags & LHAF_FP32_TERMS) != 0;
+  int occ = 0;
+  const int team = choose_team(ctx, fp32, pl, &occ);
+  if (team == 0) return LHAF_ETOOBIG;
+  TermParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.nd = pl.nd;
+  p.ld = pl.nd | 1;
+  p.bord = pl.bord;
+  p.h = pl.h;
+  p.H = pl.H;
+  p.Hl = pl.Hl;
+  p.P = pl.P;
+  p.hp = pl.hp;
+  p.hp_even = pl.hp_even;
+  p.plain = (flags & LHAF_PLAIN_ACCUM) ? 1 : 0;
+  p.n_items = pl.Hl * (pl.Hl - 1) / 2;
+  p.team_bytes = (int)team_shared_bytes(fp32, pl.nd, pl.H, pl.P);
+  p.items_bytes = (int)(cta_shared_bytes(fp32, team, pl.nd, pl.H, pl.Hl, pl.P) -
+                        (size_t)teams_per_cta(team) * p.team_bytes);
+  for (int q = 0; q < pl.P; q++) {
+    p.eta[q] = pl.eta[q];
+    p.radix[q] = pl.radix[q];
+  }
+  const uint64_t T = te > tb ? te - tb : 0;
+  const int tpc = teams_per_cta(team);
+  const uint64_t max_ctas = (uint64_t)ctx->sms * (uint64_t)occ;
+  uint64_t grid = (T + tpc - 1) / tpc;
+  if (grid > max_ctas) grid = max_ctas;
+  if (grid < 1) grid = 1;
+  p.total_teams = grid * (uint64_t)tpc;
+  if (p.total_teams > ctx->partial_cap) return LHAF_ETOOBIG;
+  p.rounds = (T + p.total_teams - 1) / p.total_teams;
+  p.t_begin = tb;
+  p.t_end = te;
+  if (timed) cudaEventRecord(ctx->ev0, ctx->stream);
+  const void* chat = fp32 ? (const void*)ctx->d_chat32 : (const void*)ctx->d_chat;
+  cudaError_t e = launch_terms(fp32, team, chat, p, (int)grid, ctx->d_partials, ctx->stream);
+  if (e != cudaSuccess) return LHAF_ECUDA;
+  e = launch_reduce(ctx->d_partials, (long long)p.total_teams, pl.h, dd_dst, val_dst, ctx->stream);
+  if (e != cudaSuccess) return LHAF_ECUDA;
+  if (timed) cudaEventRecord(ctx->ev1, ctx->stream);
+  if (stats) {
+    stats->terms = T;
+    stats->n_dim = pl.nd;
+    stats->h = pl.h;
+    stats->pairs = pl.P;
+    stats->team = team;
+    stats->flops_model = (double)T * lhaf_model_flops_per_term(pl.nd, pl.h, pl.bord);
+    stats->kernel_ms = 0.0;
+  }
+  return LHAF_OK;
+}
+
+lhaf_status lhaf_common(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128* gamma, const int32_t* reps,
+                        uint32_t flags, bool ranged, uint64_t tb, uint64_t te, lhaf_c128* out, double* partial_dd,
+                        lhaf_stats* stats) {
+  if (!ctx || M <= 0 || !B) return LHAF_EINVAL;
+  if (!ranged && !out) return LHAF_EINVAL;
+  if (ranged && !partial_dd) return LHAF_EINVAL;
+  const bool dev = (flags & LHAF_DEVICE_PTRS) != 0;
+  if (!dev) {
+    lhaf_status v = validate_host_inputs(M, B, gamma, reps);
+    if (v != LHAF_OK) return v;
+  } else if (reps) {
+    for (int i = 0; i < M; i++)
+      if (reps[i] < 0) return LHAF_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return LHAF_ECUDA;
+  Plan pl;
+  // Loop border: with host inputs, detected from gamma; with device inputs, present unless the
+  // caller declares LHAF_NO_LOOPS.
+  bool loops = !(flags & LHAF_NO_LOOPS);
+  lhaf_status st = build_plan(M, reps, flags, loops, pl);
+  if (st != LHAF_OK) return st;
+  if (!dev && loops && pl.N > 0 && !has_loops_host(pl, M, B, gamma)) {
+    st = build_plan(M, reps, flags, false, pl);
+    if (st != LHAF_OK) return st;
+  }
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (ranged) {
+    if (tb > te || te > pl.T) return LHAF_EINVAL;
+  } else {
+    tb = 0;
+    te = pl.T;
+  }
+  if (pl.N == 0) {  // empty pattern: lhaf = 1 (one empty matching)
+    if (ranged) {
+      const double v[4] = {tb < te ? 1.0 : 0.0, 0.0, 0.0, 0.0};
+      if (dev) return cudaMemcpyAsync(partial_dd, v, sizeof(v), cudaMemcpyHostToDevice, ctx->stream) == cudaSuccess
+                          ? LHAF_OK
+                          : LHAF_ECUDA;
+      std::memcpy(partial_dd, v, sizeof(v));
+      return LHAF_OK;
+    }
+    lhaf_c128 one = {1.0, 0.0};
+    if (dev) {
+      return cudaMemcpyAsync(out, &one, sizeof(one), cudaMemcpyHostToDevice, ctx->stream) == cudaSuccess ? LHAF_OK
+                                                                                                         : LHAF_ECUDA;
+    }
+    *out = one;
+    return LHAF_OK;
+  }
+  const bool fp32 = (flags & LHAF_FP32_TERMS) != 0;
+  st = stage_chat(ctx, pl, M, B, gamma, flags, fp32);
+  if (st != LHAF_OK) return st;
+  const bool timed = stats != nullptr;
+  double* dd_dst = ranged ? (dev ? partial_dd : ctx->d_out) : nullptr;
+  double2* val_dst = ranged ? nullptr : (dev ? (double2*)out : (double2*)(ctx->d_out + 4));
+  st = run_terms(ctx, pl, flags, tb, te, dd_dst, val_dst, stats, timed);
+  if (st != LHAF_OK) return st;
+  if (!dev) {
+    cudaError_t e = cudaMemcpyAsync(ctx->h_out, ctx->d_out, 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) return LHAF_ECUDA;
+  }
+  if (!dev || timed) {
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return LHAF_ECUDA;
+  }
+  if (timed) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    stats->kernel_ms = ms;
+  }
+  if (!dev) {
+    if (ranged) {
+      std::memcpy(partial_dd, ctx->h_out, 4 * sizeof(double));
+    } else {
+      out->re = ctx->h_out[4];
+      out->im = ctx->h_out[5];
+    }
+  }
+  return cudaGetLastError() == cudaSuccess ? LHAF_OK : LHAF_ECUDA;
+}
+
+}  // namespace
+
+extern "C" lhaf_status lhaf(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128* gamma, const int32_t* reps,
+                            uint32_t flags, lhaf_c128* out, lhaf_stats* stats) {
+  return lhaf_common(ctx, M, B, gamma, reps, flags, false, 0, 0, out, nullptr, stats);
+}
+
+extern "C" lhaf_status lhaf_range(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128* gamma,
+                                  const int32_t* reps, uint32_t flags, uint64_t term_begin, uint64_t term_end,
+                                  double* partial_dd, lhaf_stats* stats) {
+  return lhaf_common(ctx, M, B, gamma, reps, flags, true, term_begin, term_end, nullptr, partial_dd, stats);
+}
+
+extern "C" double lhaf_flops_per_term(int n_dim, int h, int bordered) {
+  if (n_dim < 2 || n_dim > kMaxDim || h < 1) return 0.0;
+  return lhaf_model_flops_per_term(n_dim, h, bordered ? 1 : 0);
+}

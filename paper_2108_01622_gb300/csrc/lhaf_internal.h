@@ -1,0 +1,58 @@
+// Internal declarations shared by the host planner/API and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lhafgpu {
+
+constexpr int kMaxDim = 64;      // working dimension limit (slots + loop border)
+constexpr int kMaxPairs = 32;    // pairs limit (kMaxDim / 2)
+constexpr int kMaxDegree = 256;  // h limit
+
+// Per-launch description of one loop hafnian's sieve (App. B.2-B.4), passed by value.
+struct TermParams {
+  int nd;        // working dimension (2 * P slots, + bord)
+  int ld;        // leading dimension of the shared working matrix (odd, >= nd)
+  int bord;      // 1 when the loop border (index 0) is present
+  int h;         // degree of the coefficient taken: ceil(N/2)
+  int H;         // series length: h + bord
+  int Hl;        // La Budde truncation: min(H, nd)
+  int P;         // pairs
+  int hp;        // index of the pair whose digit is halved
+  int hp_even;   // 1 when eta[hp] is even (its middle digit is counted once)
+  int plain;     // 1: plain FP64 accumulation instead of double-double
+  int n_items;   // push-item table entries: Hl (Hl - 1) / 2
+  int team_bytes;   // shared bytes per team
+  int items_bytes;  // shared bytes for the item table + 1/k table
+  int eta[kMaxPairs];
+  int radix[kMaxPairs];
+  unsigned long long t_begin, t_end;  // evaluated-term index range
+  unsigned long long rounds;          // terms per team (uniform, last round may be idle)
+  unsigned long long total_teams;
+};
+
+// Launch the FP64 (fp32 = false) or FP32 term kernel. chat is the bordered slot matrix (nd x nd,
+// row-major) in double2 (fp32 = false) or float2. partials receives 4 doubles per team.
+// Returns the number of teams launched (>0), or 0 on a launch error.
+cudaError_t launch_terms(bool fp32, int team, const void* chat, const TermParams& p, int grid,
+                         double* partials, cudaStream_t stream);
+
+// Shared bytes one CTA needs, and CTA size, for a team size.
+int cta_threads(int team);
+int teams_per_cta(int team);
+size_t team_shared_bytes(bool fp32, int nd, int H, int P);
+size_t cta_shared_bytes(bool fp32, int team, int nd, int H, int Hl, int P);
+int max_ctas_per_sm(bool fp32, int team, size_t smem_bytes);
+
+// Double-double reduction of `count` partials (4 doubles each): out_dd (4 doubles, unscaled) and
+// out_val (complex, scaled by 2^-h). Either output may be NULL.
+cudaError_t launch_reduce(const double* partials, long long count, int h, double* out_dd,
+                          double2* out_val, cudaStream_t stream);
+
+// Gather the bordered slot matrix from device B (M x M, upper triangle read) and gamma.
+// slot_mode: modes of the 2P slots (-1 = pad). gamma may be NULL (diag(B) is used).
+cudaError_t launch_gather(const double2* B, const double2* gamma, int M, const int* slot_mode_host,
+                          int P, int bord, double2* chat, float2* chat32, cudaStream_t stream);
+
+}  // namespace lhafgpu

@@ -1,0 +1,51 @@
+// Host planner for the repeated-pair finite difference sieve (arXiv:2108.01622, App. B.2-B.4).
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/lhaf.h"
+
+namespace lhafgpu {
+
+// One loop hafnian's sieve plan.
+//   pairs q = 0..P-1 with repeat counts eta[q] (greedy matching of App. B.3; a leftover photon of
+//   an odd pattern is paired with a pad index of loop weight 1);
+//   slots 2q (left photon of pair q) and 2q+1 (right photon) carry modes slot_mode[] (-1 = pad);
+//   the working dimension is nd = 2P + bord, where bord = 1 adds the loop border index 0;
+//   evaluated terms are the mixed-radix numbers over radix[q] (= eta[q] + 1 except the halved
+//   digit of pair hp), T = prod radix.
+struct Plan {
+  int M = 0, N = 0, h = 0, H = 0, Hl = 0, bord = 0, P = 0, nd = 0;
+  int hp = 0, hp_even = 0;
+  std::vector<int> slot_mode, eta, radix;
+  uint64_t T = 0;
+};
+
+lhaf_status build_plan(int M, const int32_t* reps, uint32_t flags, bool loops, Plan& pl);
+
+// Bordered slot matrix (nd x nd, row-major): [0][0] = 0; [0][1+s] = [1+s][0] = v_s (gamma of the
+// slot's mode, 1 for the pad); [b+s][b+t] = B[mode(s)][mode(t)] (0 when either is the pad), with B
+// read from its upper triangle.
+void build_chat_host(const Plan& pl, int M, const lhaf_c128* B, const lhaf_c128* gamma,
+                     std::complex<double>* chat);
+
+// Algorithmic real flops of one term of this implementation: 8 per complex multiply-add of the
+// elimination reduction, La Budde's recurrence and the series recurrences.
+double lhaf_model_flops_per_term(int nd, int h, int bord);
+
+// Modelled FP64 lane utilisation (useful lane operations / issued lane slots) for team size G.
+double model_lane_efficiency(int nd, int Hl, int h, int bord, int G);
+
+inline void dd_add_dd_host(double& hi, double& lo, double bh, double bl) {
+  const double s = hi + bh;
+  const double bb = s - hi;
+  double err = (hi - (s - bb)) + (bh - bb);
+  err += lo + bl;
+  const double t = s + err;
+  lo = err - (t - s);
+  hi = t;
+}
+
+}  // namespace lhafgpu

@@ -1,0 +1,100 @@
+"""C-ABI library without a GPU: it loads, exports every function include/lhaf.h declares, and its
+host planner (greedy pairing of App. B.3, term counts, limits, errors) agrees with the oracle."""
+import ctypes
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import lhaf_oracle as lo
+from tests.libutil import ensure_built
+
+
+@pytest.fixture(scope="module")
+def lg():
+    return ensure_built()
+
+
+def test_exports_every_declared_function(lg):
+    lib = ctypes.CDLL(lg.LIB_PATH)
+    names = lg.header_functions()
+    assert {"lhaf", "lhaf_range", "lhaf_ctx_create", "lhaf_plan"} <= set(names)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def halved_count(reps, loops):
+    """Evaluated terms after the sign-symmetry halving, from the oracle's greedy pairs."""
+    pairs, leftover = lo.matched_reps(reps)
+    etas = [e for _, _, e in pairs] + ([1] if leftover is not None else [])
+    if not etas:
+        return 1
+    odd = [e for e in etas if e % 2]
+    T = math.prod(e + 1 for e in etas)
+    if odd:
+        return T // 2
+    emax = max(etas)
+    return (T // (emax + 1)) * (emax // 2 + 1)
+
+
+@pytest.mark.parametrize("reps", list(itertools.product(range(4), repeat=3)) + [(2, 1, 0, 3), (1,) * 24, (4, 4, 4), (9,)])
+def test_plan_matches_oracle_greedy(lg, reps):
+    T, nd, h, P = lg.plan(reps, has_loops=True)
+    pairs, leftover = lo.matched_reps(reps)
+    N = sum(reps)
+    if N == 0:
+        assert T == 1
+        return
+    assert P == len(pairs) + (leftover is not None)
+    assert h == (N + 1) // 2
+    assert nd == 2 * P + 1
+    assert T == halved_count(reps, True)
+    # without loops the border disappears unless a pad is needed
+    T0, nd0, _, _ = lg.plan(reps, has_loops=False)
+    assert T0 == T
+    assert nd0 == 2 * P + (1 if leftover is not None else 0)
+
+
+def test_worked_example_halved(lg):
+    # App. B.2 example n = (2,1,0,3): 6 terms, 3 after the sign-symmetry halving
+    T, nd, h, P = lg.plan([2, 1, 0, 3], has_loops=False)
+    assert (T, P, h) == (3, 2, 3)
+
+
+def test_no_repeat_speedup_gives_duplicated_count(lg):
+    T, nd, h, P = lg.plan([2, 1, 0, 3], flags=lg.NO_REPEAT_SPEEDUP, has_loops=False)
+    assert T == 2 ** 2 and P == 3
+
+
+def test_limits_and_errors(lg):
+    with pytest.raises(lg.LhafError) as e:
+        lg.plan([1] * 70, has_loops=True)  # 35 pairs + border > 64
+    assert e.value.status == 2
+    with pytest.raises(lg.LhafError) as e:
+        lg.plan([1, -1, 2])
+    assert e.value.status == 1
+    T, nd, h, P = lg.plan([1] * 62, has_loops=True)
+    assert nd == 63 and T == 2 ** 30
+
+
+def test_flop_model_positive_and_cubic(lg):
+    f24 = lg.flops_per_term(25, 12, True)
+    f48 = lg.flops_per_term(49, 24, True)
+    assert f24 > 0 and 6.0 < f48 / f24 < 9.5
+    assert lg.flops_per_term(1, 1, False) == 0.0
+
+
+def test_combine_scales_exactly(lg):
+    parts = np.array([[3.0, 1e-20, -1.0, 0.0], [5.0, 0.0, 2.0, -1e-20]])
+    assert lg.combine(parts, 3) == complex(1.0, 0.125)
+
+
+def test_ctx_create_without_gpu_fails_cleanly(lg):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    with pytest.raises(lg.LhafError) as e:
+        lg.Context(0)
+    assert e.value.status == 3

@@ -1,0 +1,157 @@
+"""GPU parity: the CUDA sieve (through the C ABI) against the CPU oracle on the same seeded inputs.
+
+Tolerance: 1e-10 relative for the FP64 path (the paper's complex128 path, App. B.4; the oracle sums
+its fp64 terms exactly with math.fsum). Where the value is near zero by cancellation (odd N with
+gamma = 0) the bar is relative to the sum of |terms|, which the oracle supplies."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import lhaf_oracle as lo
+from paper_2108_01622_gb300 import workloads as wl
+from tests.libutil import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def lg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return ensure_built()
+
+
+@pytest.fixture(scope="module")
+def ctx(lg):
+    c = lg.Context(0)
+    yield c
+    c.close()
+
+
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+SMALL = [(2, 1, 0, 3), (4, 0, 0, 2), (3, 2, 2, 1), (1, 1, 1), (5, 0, 0, 0), (2, 2, 2, 2), (1,), (2,),
+         (3, 1), (6, 1, 1), (0, 3, 0, 4), (1, 1, 1, 1, 1, 1, 1, 1), (2, 2, 1, 1, 0, 3), (7, 5),
+         (1, 1, 1, 1, 1, 1, 1, 1, 1), (3, 3, 3, 3, 1)]
+
+
+@pytest.mark.parametrize("reps", SMALL)
+@pytest.mark.parametrize("loops", [True, False])
+def test_small_patterns_vs_oracle(ctx, reps, loops):
+    p = wl.small_problem(seed=sum(reps) + 31 * len(reps), M=len(reps), reps=reps, loops=loops)
+    ref = lo.lhaf_repeated(p.B, p.gamma, p.reps)
+    got = ctx.lhaf(p.B, p.gamma, p.reps)
+    if abs(ref) < 1e-12:
+        assert abs(got) < 1e-11
+    else:
+        assert rel(got, ref) < TOL, (got, ref)
+
+
+def test_empty_pattern_is_one(ctx):
+    p = wl.small_problem(1, 3, (0, 0, 0))
+    assert ctx.lhaf(p.B, p.gamma, p.reps) == 1.0
+
+
+@pytest.mark.parametrize("team", ["8", "16", "32", "64", "128"])
+def test_every_team_size_agrees(ctx, team, monkeypatch):
+    p = wl.single_lhaf_24(seed=11, n_photons=14)
+    ref = lo.lhaf_repeated(p.B, p.gamma, p.reps)
+    monkeypatch.setenv("LHAF_TEAM", team)
+    got, st = ctx.lhaf(p.B, p.gamma, p.reps, stats=True)
+    assert st["team"] == int(team)
+    assert rel(got, ref) < TOL
+    p2 = wl.collision_lhaf_40(seed=12, n_modes=8, n_photons=14)
+    ref2 = lo.lhaf_repeated(p2.B, p2.gamma, p2.reps)
+    assert rel(ctx.lhaf(p2.B, p2.gamma, p2.reps), ref2) < TOL
+
+
+def test_collision_free_24_photons(ctx):
+    # 24-mode Haar kernel, one photon per mode: 2^11 evaluated terms, working dimension 25
+    p = wl.single_lhaf_24(seed=1)
+    ref = lo.lhaf_repeated(p.B, p.gamma, p.reps)
+    got, st = ctx.lhaf(p.B, p.gamma, p.reps, stats=True)
+    assert st["terms"] == 2 ** 11 and st["n_dim"] == 25 and st["h"] == 12
+    assert rel(got, ref) < TOL
+
+
+def test_collision_pattern_40_photons(ctx):
+    # 100-mode Haar kernel, 40 photons over 22 modes, counts 1..4, gamma = 0
+    p = wl.collision_lhaf_40(seed=2)
+    ref = lo.lhaf_repeated(p.B, p.gamma, p.reps)
+    got, st = ctx.lhaf(p.B, p.gamma, p.reps, stats=True)
+    assert rel(got, ref) < TOL
+    # the explicit duplicated-row sieve (every photon paired singly) gives the same value
+    dup = ctx.lhaf(p.B, p.gamma, p.reps, flags=0x8)
+    assert rel(dup, ref) < TOL
+
+
+def test_odd_pattern_without_loops_is_zero(ctx):
+    p = wl.small_problem(5, 5, (3, 1, 2, 0, 1), loops=False)
+    got = ctx.lhaf(p.B, p.gamma, p.reps)
+    assert abs(got) < 1e-12
+
+
+def test_range_partials_add_up(ctx, lg):
+    p = wl.single_lhaf_24(seed=3, n_photons=18)
+    T, nd, h, P = lg.plan(p.reps)
+    full = ctx.lhaf(p.B, p.gamma, p.reps)
+    cuts = [0, 7, 100, 101, T // 2, T]
+    parts = [ctx.lhaf_range(p.B, p.gamma, p.reps, a, b) for a, b in zip(cuts[:-1], cuts[1:])]
+    assert rel(lg.combine(np.array(parts), h), full) < 1e-13
+    empty = ctx.lhaf_range(p.B, p.gamma, p.reps, 5, 5)
+    assert np.all(empty == 0)
+
+
+def test_device_pointer_path_matches_host(ctx):
+    import torch
+
+    p = wl.collision_lhaf_40(seed=7, n_modes=10, n_photons=20)
+    p.gamma = wl.complex_normal(np.random.default_rng(0), len(p.gamma))
+    host = ctx.lhaf(p.B, p.gamma, p.reps)
+    Bd = torch.from_numpy(p.B).cuda()
+    gd = torch.from_numpy(p.gamma).cuda()
+    out = ctx.lhaf(Bd, gd, p.reps)
+    torch.cuda.synchronize()
+    assert rel(complex(out.cpu()[0]), host) < 1e-14
+    ref = lo.lhaf_repeated(p.B, p.gamma, p.reps)
+    assert rel(host, ref) < TOL
+
+
+def test_gamma_none_uses_diagonal(ctx):
+    p = wl.small_problem(9, 4, (2, 1, 1, 2))
+    ref = lo.lhaf_repeated(p.B, np.diag(p.B).copy(), p.reps)
+    assert rel(ctx.lhaf(p.B, None, p.reps), ref) < TOL
+
+
+def test_invalid_inputs_are_rejected(ctx, lg):
+    p = wl.small_problem(9, 3, (1, 1, 1))
+    bad = p.B.copy()
+    bad[0, 1] = np.nan
+    with pytest.raises(lg.LhafError) as e:
+        ctx.lhaf(bad, p.gamma, p.reps)
+    assert e.value.status == 1
+    with pytest.raises(lg.LhafError) as e:
+        ctx.lhaf(p.B, p.gamma, (1, -2, 1))
+    assert e.value.status == 1
+
+
+def test_fp32_terms_stated_error(ctx):
+    # FP32 per-term arithmetic, double-double accumulation: error stated against the FP64 oracle
+    p = wl.single_lhaf_24(seed=1, n_photons=16)
+    ref = lo.lhaf_repeated(p.B, p.gamma, p.reps)
+    got = ctx.lhaf(p.B, p.gamma, p.reps, flags=0x2)
+    assert rel(got, ref) < 1e-3
+
+
+def test_plain_accumulation_close(ctx):
+    p = wl.single_lhaf_24(seed=1)
+    a = ctx.lhaf(p.B, p.gamma, p.reps)
+    b = ctx.lhaf(p.B, p.gamma, p.reps, flags=0x4)
+    assert rel(b, a) < 1e-11
