@@ -123,6 +123,27 @@ double lhaf_flops_per_term(int n_dim, int h, int bordered);
  * by 2^-h (exact). */
 lhaf_status lhaf_combine(int count, const double* partials_dd, int32_t h, lhaf_c128* out);
 
+/* Allocation-free lhaf (no counterpart in the paper). For callers that cannot call cudaMalloc or
+ * cudaFree: code where another allocator (a framework's caching allocator, a pre-reserved memory
+ * pool) owns the device memory, or loops that must not take the implicit device synchronisation of
+ * an allocation. Same result as lhaf() with LHAF_DEVICE_PTRS, without a context.
+ *   device      : the GPU to run on (made current for the call, the previous device is restored).
+ *   cuda_stream : cudaStream_t the work is ordered on (NULL = legacy default stream); the call
+ *                 returns without synchronising.
+ *   B, gamma    : DEVICE pointers as for lhaf() (gamma may be NULL); reps: HOST pointer.
+ *   out         : DEVICE pointer to one lhaf_c128.
+ *   flags       : LHAF_FP32_TERMS, LHAF_PLAIN_ACCUM, LHAF_NO_REPEAT_SPEEDUP, LHAF_NO_LOOPS.
+ * Scratch: a fixed 224 KiB device array inside the library (slot matrix for working dimension
+ * <= LHAF_MAX_DIM plus partial sums of at most 4096 GPU teams), held by every GPU that loads the
+ * library until the process exits. Larger problems are rejected with LHAF_ETOOBIG; the number of
+ * terms is not limited (teams loop over more terms). The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it, so make that first call before any
+ * stream capture. All calls share the one array and it keeps the last call's contents (nothing in
+ * it needs to start at zero): calls that overlap on the GPU, e.g. on two streams, race and give
+ * wrong results; order them on one stream or synchronise between them. */
+lhaf_status lhaf_noalloc(int device, void* cuda_stream, int M, const lhaf_c128* B, const lhaf_c128* gamma,
+                         const int32_t* reps, uint32_t flags, lhaf_c128* out);
+
 /* Measurement utility (no counterpart in the paper): FP64 fused multiply-add throughput of
  * `device` in GFLOP/s (2 flops per FMA), from independent FMA chains over every SM for a few tens
  * of milliseconds. The sieve kernels are bound by this rate; it is the roofline denominator. */
