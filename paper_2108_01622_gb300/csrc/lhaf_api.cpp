@@ -29,6 +29,9 @@ struct lhaf_ctx {
   double* d_partials = nullptr;
   size_t partial_cap = 0;  // teams
   double* d_out = nullptr;  // 4 dd doubles + 2 value doubles
+  void* d_stage = nullptr;  // staged characteristic polynomials (series_kernel input)
+  double* d_wstage = nullptr;
+  size_t stage_bytes = 0, wstage_terms = 0;
   // pinned host staging
   double2* h_chat = nullptr;
   float2* h_chat32 = nullptr;
@@ -60,6 +63,8 @@ extern "C" void lhaf_ctx_destroy(lhaf_ctx* ctx) {
   cudaFree(ctx->d_chat32);
   cudaFree(ctx->d_partials);
   cudaFree(ctx->d_out);
+  cudaFree(ctx->d_stage);
+  cudaFree(ctx->d_wstage);
   cudaFreeHost(ctx->h_chat);
   cudaFreeHost(ctx->h_chat32);
   cudaFreeHost(ctx->h_out);
@@ -141,7 +146,7 @@ bool finite_c(const lhaf_c128& z) { return std::isfinite(z.re) && std::isfinite(
 
 // Choose the lanes-per-term team size: a model of FP64 lane utilisation times the share of the
 // four SM sub-partitions that hold at least one warp. LHAF_TEAM in the environment overrides.
-int choose_team(lhaf_ctx* ctx, bool fp32, const Plan& pl, int* ctas_per_sm) {
+int choose_team(lhaf_ctx* ctx, bool fp32, const Plan& pl, bool staged, int* ctas_per_sm) {
   const char* env = std::getenv("LHAF_TEAM");
   int forced = env ? std::atoi(env) : 0;
   const int cands[5] = {8, 16, 32, 64, 128};
@@ -149,9 +154,9 @@ int choose_team(lhaf_ctx* ctx, bool fp32, const Plan& pl, int* ctas_per_sm) {
   int best_g = 32, best_occ = 0;
   for (int g : cands) {
     if (forced && g != forced) continue;
-    const size_t smem = cta_shared_bytes(fp32, g, pl.nd, pl.H, pl.Hl, pl.P);
+    const size_t smem = cta_shared_bytes(fp32, g, pl.nd, pl.H, pl.Hl, pl.P, staged);
     if (smem > 227 * 1024) continue;
-    const int occ = max_ctas_per_sm(fp32, g, smem);
+    const int occ = max_ctas_per_sm(fp32, g, smem, staged);
     if (occ <= 0) continue;
     const double warps = (double)occ * cta_threads(g) / 32.0;
     const double cover = std::min(1.0, warps / 4.0);
@@ -217,13 +222,52 @@ lhaf_status validate_host_inputs(int M, const lhaf_c128* B, const lhaf_c128* gam
   return LHAF_OK;
 }
 
+// Staging buffer for the series kernel: grown on demand (terms x coefficient rows).
+constexpr size_t kStageBytesMax = (size_t)256 << 20;
+
+bool ensure_stage(lhaf_ctx* ctx, size_t bytes, size_t terms) {
+  if (ctx->stage_bytes >= bytes && ctx->wstage_terms >= terms) return true;
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(ctx->d_stage);
+  cudaFree(ctx->d_wstage);
+  ctx->d_stage = nullptr;
+  ctx->d_wstage = nullptr;
+  ctx->stage_bytes = ctx->wstage_terms = 0;
+  if (cudaMalloc(&ctx->d_stage, bytes) != cudaSuccess || cudaMalloc(&ctx->d_wstage, terms * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(ctx->d_stage);
+    ctx->d_stage = nullptr;
+    return false;
+  }
+  ctx->stage_bytes = bytes;
+  ctx->wstage_terms = terms;
+  return true;
+}
+
 // Runs the sieve over [tb, te) of the plan; writes the dd partial (unscaled) and/or the scaled
-// value into device buffers dd_dst / val_dst.
+// value into device buffers dd_dst / val_dst. Degrees up to kStageMaxDegree stage the term
+// polynomials and finish them one term per thread (series_kernel), in chunks of term ranges that
+// fit the staging buffer; larger degrees finish each term inside the term kernel.
 lhaf_status run_terms(lhaf_ctx* ctx, const Plan& pl, uint32_t flags, uint64_t tb, uint64_t te, double* dd_dst,
                       double2* val_dst, lhaf_stats* stats, bool timed) {
   const bool fp32 = (flags & LHAF_FP32_TERMS) != 0;
+  const char* env_stage = std::getenv("LHAF_STAGE");
+  bool staged = pl.h <= kStageMaxDegree && !(env_stage && env_stage[0] == '0');
+  const size_t cs = fp32 ? sizeof(float2) : sizeof(double2);
+  const int rows = pl.bord ? 2 * pl.h + 1 : pl.h;
+  const uint64_t T = te > tb ? te - tb : 0;
+  uint64_t chunk = T;
+  if (staged) {
+    const uint64_t cap = kStageBytesMax / ((size_t)rows * cs);
+    chunk = std::min<uint64_t>(T, cap);
+    const uint64_t series_cap = (uint64_t)ctx->partial_cap * 64;  // series blocks of 64 terms
+    chunk = std::min<uint64_t>(chunk, series_cap);
+    if (chunk < 1) chunk = 1;
+    if (!ensure_stage(ctx, (size_t)rows * cs * chunk, chunk)) staged = false;
+    if (!staged) chunk = T;
+  }
   int occ = 0;
-  const int team = choose_team(ctx, fp32, pl, &occ);
+  const int team = choose_team(ctx, fp32, pl, staged, &occ);
   if (team == 0) return LHAF_ETOOBIG;
   TermParams p;
   std::memset(&p, 0, sizeof(p));
@@ -238,30 +282,54 @@ lhaf_status run_terms(lhaf_ctx* ctx, const Plan& pl, uint32_t flags, uint64_t tb
   p.hp_even = pl.hp_even;
   p.plain = (flags & LHAF_PLAIN_ACCUM) ? 1 : 0;
   p.n_items = pl.Hl * (pl.Hl - 1) / 2;
-  p.team_bytes = (int)team_shared_bytes(fp32, pl.nd, pl.H, pl.P);
-  p.items_bytes = (int)(cta_shared_bytes(fp32, team, pl.nd, pl.H, pl.Hl, pl.P) -
+  p.team_bytes = (int)team_shared_bytes(fp32, pl.nd, pl.H, pl.P, staged);
+  p.items_bytes = (int)(cta_shared_bytes(fp32, team, pl.nd, pl.H, pl.Hl, pl.P, staged) -
                         (size_t)teams_per_cta(team) * p.team_bytes);
   for (int q = 0; q < pl.P; q++) {
     p.eta[q] = pl.eta[q];
     p.radix[q] = pl.radix[q];
   }
-  const uint64_t T = te > tb ? te - tb : 0;
   const int tpc = teams_per_cta(team);
   const uint64_t max_ctas = (uint64_t)ctx->sms * (uint64_t)occ;
-  uint64_t grid = (T + tpc - 1) / tpc;
-  if (grid > max_ctas) grid = max_ctas;
-  if (grid < 1) grid = 1;
-  p.total_teams = grid * (uint64_t)tpc;
-  if (p.total_teams > ctx->partial_cap) return LHAF_ETOOBIG;
-  p.rounds = (T + p.total_teams - 1) / p.total_teams;
-  p.t_begin = tb;
-  p.t_end = te;
+  double* acc_dd = dd_dst ? dd_dst : ctx->d_out;  // running double-double sum over chunks
   if (timed) cudaEventRecord(ctx->ev0, ctx->stream);
   const void* chat = fp32 ? (const void*)ctx->d_chat32 : (const void*)ctx->d_chat;
-  cudaError_t e = launch_terms(fp32, team, chat, p, (int)grid, ctx->d_partials, ctx->stream);
-  if (e != cudaSuccess) return LHAF_ECUDA;
-  e = launch_reduce(ctx->d_partials, (long long)p.total_teams, pl.h, dd_dst, val_dst, ctx->stream);
-  if (e != cudaSuccess) return LHAF_ECUDA;
+  uint64_t c0 = tb;
+  int ci = 0;
+  do {
+    const uint64_t c1 = std::min<uint64_t>(te, c0 + chunk);
+    const uint64_t n = c1 - c0;
+    uint64_t grid = (n + tpc - 1) / tpc;
+    if (grid > max_ctas) grid = max_ctas;
+    if (grid < 1) grid = 1;
+    p.total_teams = grid * (uint64_t)tpc;
+    if (!staged && p.total_teams > ctx->partial_cap) return LHAF_ETOOBIG;
+    p.rounds = (n + p.total_teams - 1) / p.total_teams;
+    p.t_begin = c0;
+    p.t_end = c1;
+    cudaError_t e;
+    long long nparts;
+    if (n == 0) {
+      nparts = 0;  // empty range: the reduction writes a zero partial
+    } else if (staged) {
+      e = launch_terms(fp32, team, chat, p, (int)grid, ctx->d_partials, ctx->stream, ctx->d_stage, ctx->d_wstage,
+                       (long long)chunk);
+      if (e != cudaSuccess) return LHAF_ECUDA;
+      e = launch_series(fp32, ctx->d_stage, ctx->d_wstage, (long long)n, (long long)chunk, pl.h, pl.bord, p.plain,
+                        ctx->d_partials, ctx->stream);
+      if (e != cudaSuccess) return LHAF_ECUDA;
+      nparts = series_blocks((long long)n);
+    } else {
+      e = launch_terms(fp32, team, chat, p, (int)grid, ctx->d_partials, ctx->stream);
+      if (e != cudaSuccess) return LHAF_ECUDA;
+      nparts = (long long)p.total_teams;
+    }
+    const bool last = c1 >= te;
+    e = launch_reduce(ctx->d_partials, nparts, pl.h, acc_dd, last ? val_dst : nullptr, ctx->stream, ci > 0 ? 1 : 0);
+    if (e != cudaSuccess) return LHAF_ECUDA;
+    c0 = c1;
+    ci++;
+  } while (c0 < te);
   if (timed) cudaEventRecord(ctx->ev1, ctx->stream);
   if (stats) {
     stats->terms = T;

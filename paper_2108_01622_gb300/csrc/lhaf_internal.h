@@ -33,22 +33,34 @@ struct TermParams {
 };
 
 // Launch the FP64 (fp32 = false) or FP32 term kernel. chat is the bordered slot matrix (nd x nd,
-// row-major) in double2 (fp32 = false) or float2. partials receives 4 doubles per team.
-// Returns the number of teams launched (>0), or 0 on a launch error.
+// row-major) in double2 (fp32 = false) or float2. Without `stage` every team finishes its terms
+// and writes 4 doubles (its double-double partial) to partials. With `stage`, each term's
+// characteristic-polynomial coefficients go to stage (coefficient-major, stage_ld terms per row,
+// term index t - t_begin) and its weight to wstage; series_kernel finishes them.
 cudaError_t launch_terms(bool fp32, int team, const void* chat, const TermParams& p, int grid,
-                         double* partials, cudaStream_t stream);
+                         double* partials, cudaStream_t stream, void* stage = nullptr,
+                         double* wstage = nullptr, long long stage_ld = 0);
 
 // Shared bytes one CTA needs, and CTA size, for a team size.
 int cta_threads(int team);
 int teams_per_cta(int team);
-size_t team_shared_bytes(bool fp32, int nd, int H, int P);
-size_t cta_shared_bytes(bool fp32, int team, int nd, int H, int Hl, int P);
-int max_ctas_per_sm(bool fp32, int team, size_t smem_bytes);
+size_t team_shared_bytes(bool fp32, int nd, int H, int P, bool staged = false);
+size_t cta_shared_bytes(bool fp32, int team, int nd, int H, int Hl, int P, bool staged = false);
+int max_ctas_per_sm(bool fp32, int team, size_t smem_bytes, bool staged = false);
 
-// Double-double reduction of `count` partials (4 doubles each): out_dd (4 doubles, unscaled) and
-// out_val (complex, scaled by 2^-h). Either output may be NULL.
+// Staged series: count terms (one per thread), partials: 4 doubles per block.
+constexpr int kStageMaxDegree = 24;
+size_t series_shared_bytes(bool fp32, int h);
+long long series_blocks(long long count);
+cudaError_t launch_series(bool fp32, const void* stage, const double* wstage, long long count,
+                          long long stage_ld, int h, int bord, int plain, double* partials,
+                          cudaStream_t stream);
+
+// Double-double reduction of `count` partials (4 doubles each): out_dd (4 doubles, unscaled; with
+// accumulate != 0 added to its previous content) and out_val (complex, scaled by 2^-h). Either
+// output may be NULL.
 cudaError_t launch_reduce(const double* partials, long long count, int h, double* out_dd,
-                          double2* out_val, cudaStream_t stream);
+                          double2* out_val, cudaStream_t stream, int accumulate = 0);
 
 // Gather the bordered slot matrix from device B (M x M, upper triangle read) and gamma.
 // slot_mode: modes of the 2P slots (-1 = pad). gamma may be NULL (diag(B) is used).

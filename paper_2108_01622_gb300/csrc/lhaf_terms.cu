@@ -14,9 +14,12 @@
 // elimination with partial pivoting): half the multiply-adds of Householder reflectors.
 //
 // A team of G lanes evaluates one term at a time with its working matrix in shared memory; a CTA
-// holds 128 / G teams (G < 32) or one team of G lanes (G >= 32). Every FP64 instruction issues at
-// one warp instruction per ~64 cycles per SM sub-partition on this part, and idle lanes cost the
-// same as busy ones, so each phase spreads its independent multiply-adds over all G lanes.
+// is one warp holding 32 / G teams (G <= 32) or one team of G lanes (G > 32). Every FP64
+// instruction issues at one warp instruction per ~64 cycles per SM sub-partition on this part,
+// and idle lanes cost the same as busy ones, so each phase spreads its independent multiply-adds
+// over all G lanes. The last step (three short sequential recurrences per term) either runs in
+// the team (inline) or is staged to global memory and run one term per thread by series_kernel,
+// where it needs no cross-lane reductions.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -71,47 +74,51 @@ __device__ __forceinline__ unsigned long long mag_key(float2 z) {
   return a > b ? a : b;
 }
 
-// 1 / z with the exponent of max(|re|, |im|) scaled out first (exact power-of-two scaling), so
-// neither |z|^2 nor its reciprocal leaves the representable range. Returns 0 for z == 0.
+// 1 / z. The exponent of max(|re|, |im|) is scaled out first (exact power-of-two scaling), so
+// d = |z s|^2 lies in [1, 8). 1/d: FP32 reciprocal seed refined by two Newton-Raphson steps
+// r <- r (2 - d r) (relative error ~2^-23 -> ~2^-46 -> below 2^-53). Returns 0 for z == 0.
 __device__ __forceinline__ double2 crecip(double2 z) {
-  unsigned long long k = mag_key(z);
+  const unsigned long long k = mag_key(z);
   if (k == 0ull) return make_double2(0.0, 0.0);
-  int e = (int)(k >> 52);          // biased exponent of the larger part (0 for subnormals)
+  int e = (int)(k >> 52);  // biased exponent of the larger part (0 for subnormals)
   if (e < 1) e = 1;
   if (e > 2045) e = 2045;
-  double sc = __longlong_as_double((long long)(2046 - e) << 52);  // 2^(1023 - (e - 1023))
-  double xs = z.x * sc, ys = z.y * sc;
-  double d = fma(xs, xs, ys * ys);
-  double rd = __drcp_rn(d);
-  return make_double2(xs * rd * sc, flip(ys) * rd * sc);
+  const double sc = __longlong_as_double((long long)(2046 - e) << 52);  // 2^(1023 - (e - 1023))
+  const double xs = z.x * sc, ys = z.y * sc;
+  const double d = fma(xs, xs, ys * ys);
+  double r = (double)__frcp_rn((float)d);
+  r = fma(r, fma(-d, r, 1.0), r);
+  r = fma(r, fma(-d, r, 1.0), r);
+  const double rs = r * sc;
+  return make_double2(xs * rs, flip(ys) * rs);
 }
 __device__ __forceinline__ float2 crecip(float2 z) {
-  unsigned k = (unsigned)mag_key(z);
+  const unsigned k = (unsigned)mag_key(z);
   if (k == 0u) return make_float2(0.f, 0.f);
   int e = (int)(k >> 23);
   if (e < 1) e = 1;
   if (e > 253) e = 253;
-  float sc = __int_as_float((253 - e + 1) << 23);  // 2^(127 - (e - 127)) clamped
-  float xs = z.x * sc, ys = z.y * sc;
-  float d = fmaf(xs, xs, ys * ys);
-  float rd = __frcp_rn(d);
-  return make_float2(xs * rd * sc, flip(ys) * rd * sc);
+  const float sc = __int_as_float((254 - e) << 23);  // 2^(127 - (e - 127))
+  const float xs = z.x * sc, ys = z.y * sc;
+  const float d = fmaf(xs, xs, ys * ys);
+  const float rs = __frcp_rn(d) * sc;
+  return make_float2(xs * rs, flip(ys) * rs);
 }
 
 // Double-double accumulation (Knuth's TwoSum).
 __device__ __forceinline__ void dd_add(double& hi, double& lo, double x) {
-  double s = hi + x;
-  double bb = s - hi;
-  double err = (hi - (s - bb)) + (x - bb);
+  const double s = hi + x;
+  const double bb = s - hi;
+  const double err = (hi - (s - bb)) + (x - bb);
   hi = s;
   lo += err;
 }
 __device__ __forceinline__ void dd_add_dd(double& hi, double& lo, double bh, double bl) {
-  double s = hi + bh;
-  double bb = s - hi;
+  const double s = hi + bh;
+  const double bb = s - hi;
   double err = (hi - (s - bb)) + (bh - bb);
   err += lo + bl;
-  double t = s + err;  // FastTwoSum renormalisation
+  const double t = s + err;  // FastTwoSum renormalisation
   lo = err - (t - s);
   hi = t;
 }
@@ -124,7 +131,7 @@ template <int G> __device__ __forceinline__ void team_sync() {
   }
 }
 
-__host__ __device__ constexpr int cta_of(int G) { return G < 32 ? 128 : G; }
+__host__ __device__ constexpr int cta_of(int G) { return G < 32 ? 32 : G; }
 
 // C(n, k): exact in 64-bit integers for n <= 62, else rounded (the weight only feeds a product).
 __device__ __forceinline__ double binom_d(int n, int k) {
@@ -145,17 +152,23 @@ __device__ __forceinline__ double binom_d(int n, int k) {
 struct TeamScratch {  // small per-team area
   unsigned long long key[4];
   int row[4];
+  double pvx[4], pvy[4];
   double weight;
   int delta[kMaxPairs];
 };
 
-template <typename R, int G>
+// ---------------------------------------------------------------------------------------------
+// The sieve terms. STAGE: write d_M and d_M - d_K per term to `stage` (coefficient-major,
+// stage_ld terms per row) and the weight to `wstage`, instead of finishing the term here.
+// ---------------------------------------------------------------------------------------------
+template <typename R, int G, bool STAGE>
 __global__ void __launch_bounds__(cta_of(G))
-terms_kernel(const typename Cx<R>::t* __restrict__ chat, const TermParams p, double* __restrict__ partials) {
+terms_kernel(const typename Cx<R>::t* __restrict__ chat, const TermParams p, double* __restrict__ partials,
+             typename Cx<R>::t* __restrict__ stage, double* __restrict__ wstage, long long stage_ld) {
   using V = typename Cx<R>::t;
   constexpr int CTA = cta_of(G);
   constexpr int TEAMS = CTA / G;
-  constexpr int SG = G < 32 ? G : 32;  // lanes that run the series recurrences
+  constexpr int SG = G < 32 ? G : 32;  // lanes of the first warp of a team
   extern __shared__ __align__(16) unsigned char smem[];
 
   const int nd = p.nd, ld = p.ld, bord = p.bord, h = p.h, H = p.H, Hl = p.Hl, P = p.P;
@@ -167,13 +180,13 @@ terms_kernel(const typename Cx<R>::t* __restrict__ chat, const TermParams p, dou
   R* invk = reinterpret_cast<R*>(smem + ((p.n_items * 2 + 15) & ~15));
   unsigned char* tb = smem + p.items_bytes + (size_t)team * p.team_bytes;
   V* W = reinterpret_cast<V*>(tb);
-  V* Sa = W + nd * ld;  // series arrays, H + 2 entries each
+  V* Sa = W + nd * ld;  // inline series arrays, H + 2 entries each (absent when staging)
   V* Sc = Sa + (H + 2);
   V* SR = Sc + (H + 2);
   V* Sp = SR + (H + 2);
   V* Sz = Sp + (H + 2);
   V* Se = Sz + (H + 2);
-  TeamScratch* ts = reinterpret_cast<TeamScratch*>(Se + (H + 2));
+  TeamScratch* ts = reinterpret_cast<TeamScratch*>(STAGE ? (void*)(W + nd * ld) : (void*)(Se + (H + 2)));
 
   // Push items (d, e) of La Budde's recurrence, sorted by e then d: 2 <= d, d + e <= Hl.
   for (int w = tid; w < p.n_items; w += CTA) {
@@ -198,92 +211,119 @@ terms_kernel(const typename Cx<R>::t* __restrict__ chat, const TermParams p, dou
     if (!valid) t = p.t_begin;
 
     // ---- digits k_i of the term, delta'_i = eta_i - 2 k_i, and the weight (App. B.4) ----
-    if (lt == 0) {
-      unsigned long long x = t;
-      double w = valid ? 1.0 : 0.0;
-      int parity = 0;
-      for (int q = 0; q < P; q++) {
-        const unsigned long long rad = (unsigned long long)p.radix[q];
-        const int k = (int)(x % rad);
-        x /= rad;
+    // Lane q of the first warp of the team decodes digit q; the weight is a product over lanes.
+    if (G <= 32 || lt < 32) {
+      double wq = 1.0;
+      int par = 0;
+      for (int q = lt; q < P; q += SG) {
+        unsigned long long st = 1ull;
+        for (int u = 0; u < q; u++) st *= (unsigned long long)p.radix[u];
+        const unsigned rad = (unsigned)p.radix[q];
+        unsigned long long qt;
+        if (t <= 0xffffffffull && st <= 0xffffffffull) {
+          qt = (unsigned)t / (unsigned)st;
+        } else {
+          qt = t / st;
+        }
+        const int k = (int)(qt % rad);
         const int eta = p.eta[q];
-        w *= binom_d(eta, k);
-        parity ^= (k & 1);
+        wq *= binom_d(eta, k);
+        par ^= (k & 1);
         ts->delta[q] = eta - 2 * k;
-        if (q == p.hp && !(p.hp_even && 2 * k == eta)) w *= 2.0;  // sign-symmetry halving
+        if (q == p.hp && !(p.hp_even && 2 * k == eta)) wq *= 2.0;  // sign-symmetry halving
       }
-      ts->weight = parity ? -w : w;
+#pragma unroll
+      for (int off = SG / 2; off >= 1; off >>= 1) {
+        wq *= __shfl_xor_sync(0xffffffffu, wq, off);
+        par ^= __shfl_xor_sync(0xffffffffu, par, off);
+      }
+      if (lt == 0) ts->weight = valid ? (par ? -wq : wq) : 0.0;
     }
     team_sync<G>();
 
     // ---- working matrix K[i][j] = Chat[i][partner(j)] * delta_hat(j) ----
-    for (int w = lt; w < nd * nd; w += G) {
-      const int i = w / nd, j = w - i * nd;
-      int jj = j, dl = 1;
-      if (j >= bord) {
-        const int s = j - bord;
-        jj = bord + (s ^ 1);
-        dl = ts->delta[s >> 1];
+    {
+      const int si = G / nd, sj = G - (G / nd) * nd;
+      int i = lt / nd, j = lt - (lt / nd) * nd;
+      for (int w = lt; w < nd * nd; w += G) {
+        int jj = j, dl = 1;
+        if (j >= bord) {
+          const int s = j - bord;
+          jj = bord + (s ^ 1);
+          dl = ts->delta[s >> 1];
+        }
+        V c = chat[i * nd + jj];
+        if (dl == -1) {
+          c.x = flip(c.x);
+          c.y = flip(c.y);
+        } else if (dl != 1) {
+          const R f = (R)dl;
+          c.x *= f;
+          c.y *= f;
+        }
+        W[i * ld + j] = c;
+        i += si;
+        j += sj;
+        if (j >= nd) {
+          j -= nd;
+          i++;
+        }
       }
-      V c = chat[i * nd + jj];
-      if (dl == -1) {
-        c.x = flip(c.x);
-        c.y = flip(c.y);
-      } else if (dl != 1) {
-        const R f = (R)dl;
-        c.x *= f;
-        c.y *= f;
-      }
-      W[i * ld + j] = c;
     }
     team_sync<G>();
 
     // ---- Hessenberg form by elimination with partial pivoting (fixes index 0) ----
     for (int k = 0; k < nd - 2; k++) {
+      // pivot: largest max(|re|, |im|) in column k below the diagonal (ties: lowest row); its
+      // value travels with the reduction
       unsigned long long key = 0ull;
       int row = k + 1;
+      V pv = zero;
       for (int i = k + 1 + lt; i < nd; i += G) {
-        const unsigned long long kk = mag_key(W[i * ld + k]);
+        const V z = W[i * ld + k];
+        const unsigned long long kk = mag_key(z);
         if (kk > key) {
           key = kk;
           row = i;
+          pv = z;
         }
       }
-      if constexpr (G <= 32) {
 #pragma unroll
-        for (int off = G / 2; off >= 1; off >>= 1) {
-          const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, off);
-          const int orow = __shfl_xor_sync(0xffffffffu, row, off);
-          if (ok > key || (ok == key && orow < row)) {
-            key = ok;
-            row = orow;
-          }
+      for (int off = SG / 2; off >= 1; off >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, off);
+        const int orow = __shfl_xor_sync(0xffffffffu, row, off);
+        const R ox = __shfl_xor_sync(0xffffffffu, pv.x, off);
+        const R oy = __shfl_xor_sync(0xffffffffu, pv.y, off);
+        if (ok > key || (ok == key && orow < row)) {
+          key = ok;
+          row = orow;
+          pv.x = ox;
+          pv.y = oy;
         }
-      } else {
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) {
-          const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, off);
-          const int orow = __shfl_xor_sync(0xffffffffu, row, off);
-          if (ok > key || (ok == key && orow < row)) {
-            key = ok;
-            row = orow;
-          }
-        }
+      }
+      if constexpr (G > 32) {
         if ((lt & 31) == 0) {
           ts->key[lt >> 5] = key;
           ts->row[lt >> 5] = row;
+          ts->pvx[lt >> 5] = (double)pv.x;
+          ts->pvy[lt >> 5] = (double)pv.y;
         }
         __syncthreads();
         key = ts->key[0];
         row = ts->row[0];
+        pv.x = (R)ts->pvx[0];
+        pv.y = (R)ts->pvy[0];
         for (int q = 1; q < G / 32; q++) {
           if (ts->key[q] > key || (ts->key[q] == key && ts->row[q] < row)) {
             key = ts->key[q];
             row = ts->row[q];
+            pv.x = (R)ts->pvx[q];
+            pv.y = (R)ts->pvy[q];
           }
         }
       }
       const int r = row;
+      const V ip = crecip(pv);  // issued before the swaps, so its latency overlaps them
       // swap rows r and k+1 (columns k..nd-1), then columns r and k+1: a similarity transform
       for (int j = k + lt; j < nd; j += G) {
         const V a = W[r * ld + j], b = W[(k + 1) * ld + j];
@@ -298,25 +338,81 @@ terms_kernel(const typename Cx<R>::t* __restrict__ chat, const TermParams p, dou
       }
       team_sync<G>();
       // multipliers l_i = K[i][k] / K[k+1][k], kept in column k below the subdiagonal
-      const V ip = crecip(W[(k + 1) * ld + k]);
       for (int i = k + 2 + lt; i < nd; i += G) W[i * ld + k] = cmul(W[i * ld + k], ip);
       team_sync<G>();
-      // rows: K[i][j] -= l_i K[k+1][j] for i >= k+2, j >= k+1
+      // rows: K[i][j] -= l_i K[k+1][j] for i >= k+2, j >= k+1. Flattened over the team, two
+      // items per lane per pass (loads of both before either store), indices advanced without
+      // division.
       const int cols = nd - k - 1;
       const int nrc = (cols - 1) * cols;
-      for (int w = lt; w < nrc; w += G) {
-        const int ii = w / cols;
-        const int i = k + 2 + ii, j = k + 1 + (w - ii * cols);
-        V a = W[i * ld + j];
-        cmsub(a, W[i * ld + k], W[(k + 1) * ld + j]);
-        W[i * ld + j] = a;
+      {
+        const int si = G / cols, sj = G - (G / cols) * cols;
+        int ii = lt / cols, jj = lt - (lt / cols) * cols;
+        for (int w = lt; w < nrc; w += 2 * G) {
+          int ii2 = ii + si, jj2 = jj + sj;
+          if (jj2 >= cols) {
+            jj2 -= cols;
+            ii2++;
+          }
+          const bool two = (w + G) < nrc;
+          V* p1 = W + (k + 2 + ii) * ld + (k + 1 + jj);
+          V* p2 = W + (k + 2 + ii2) * ld + (k + 1 + jj2);
+          V a1 = *p1;
+          const V l1 = W[(k + 2 + ii) * ld + k], r1 = W[(k + 1) * ld + k + 1 + jj];
+          V a2 = zero, l2 = zero, r2 = zero;
+          if (two) {
+            a2 = *p2;
+            l2 = W[(k + 2 + ii2) * ld + k];
+            r2 = W[(k + 1) * ld + k + 1 + jj2];
+          }
+          cmsub(a1, l1, r1);
+          cmsub(a2, l2, r2);
+          *p1 = a1;
+          if (two) *p2 = a2;
+          ii = ii2 + si;
+          jj = jj2 + sj;
+          if (jj >= cols) {
+            jj -= cols;
+            ii++;
+          }
+        }
       }
       team_sync<G>();
-      // columns: K[i][k+1] += sum_{j >= k+2} K[i][j] l_j
-      for (int i = lt; i < nd; i += G) {
-        V a = W[i * ld + k + 1];
-        for (int j = k + 2; j < nd; j++) cmac(a, W[i * ld + j], W[j * ld + k]);
-        W[i * ld + k + 1] = a;
+      // columns: K[i][k+1] += sum_{j >= k+2} K[i][j] l_j. One lane per row, or, when it fills the
+      // team better, two lanes per row (halves of the dot product, combined by one shuffle).
+      {
+        const int L = nd - k - 2;
+        const int half = (L + 1) >> 1;
+        const int slots1 = ((nd + G - 1) / G) * L;
+        const int slots2 = ((2 * nd + G - 1) / G) * (half + 1);
+        if (L >= 4 && slots2 < slots1) {
+          for (int base = 0; base < nd; base += G / 2) {
+            const int i = base + (lt >> 1);
+            const int sgm = lt & 1;
+            V acc = zero;
+            if (i < nd) {
+              const int j0 = k + 2 + sgm * half;
+              const int j1 = sgm ? nd : k + 2 + half;
+#pragma unroll 4
+              for (int j = j0; j < j1; j++) cmac(acc, W[i * ld + j], W[j * ld + k]);
+            }
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+            if (i < nd && sgm == 0) {
+              V a = W[i * ld + k + 1];
+              a.x += acc.x;
+              a.y += acc.y;
+              W[i * ld + k + 1] = a;
+            }
+          }
+        } else {
+          for (int i = lt; i < nd; i += G) {
+            V a = W[i * ld + k + 1];
+#pragma unroll 4
+            for (int j = k + 2; j < nd; j++) cmac(a, W[i * ld + j], W[j * ld + k]);
+            W[i * ld + k + 1] = a;
+          }
+        }
       }
       team_sync<G>();
     }
@@ -346,32 +442,53 @@ terms_kernel(const typename Cx<R>::t* __restrict__ chat, const TermParams p, dou
       const int E = min(deg, Hl - 2);
       const int np = (E >= 0) ? (E + 1) * (Hl - 1) - E * (E + 1) / 2 : 0;
       const int nq = min(Hl, nd - l);
-      for (int w = lt; w < np + nq; w += G) {
-        if (w < np) {
-          // push q_{l+1} into the accumulator of q_j, j = l - d + 1
-          const int it = items[w];
-          const int d = it >> 8, e = it & 255;
-          const int j = l - d + 1;
-          if (j >= 0) {
-            const V Pe = (e == 0) ? one : W[(l + e) * ld + l + 1];
-            V a = W[(l + e) * ld + j];
-            cmsub(a, W[j * ld + l], Pe);
-            W[(l + e) * ld + j] = a;
+      // Every item is dst <- a - b c: a push into acc_j, or the update of q_l[m]. Two items per
+      // lane per pass, loads first.
+      for (int w = lt; w < np + nq; w += 2 * G) {
+        V* dst[2];
+        V a[2], b[2], c[2];
+        bool ok[2];
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+          const int x = w + u * G;
+          ok[u] = false;
+          dst[u] = W;
+          a[u] = zero;
+          b[u] = zero;
+          c[u] = zero;
+          if (x < np) {
+            // push q_{l+1} into the accumulator of q_j, j = l - d + 1
+            const int it = items[x];
+            const int d = it >> 8, e = it & 255;
+            const int j = l - d + 1;
+            if (j >= 0) {
+              ok[u] = true;
+              dst[u] = W + (l + e) * ld + j;
+              a[u] = *dst[u];
+              b[u] = W[j * ld + l];
+              c[u] = (e == 0) ? one : W[(l + e) * ld + l + 1];
+            }
+          } else if (x < np + nq) {
+            // q_l[m] = q_{l+1}[m] - K_ll q_{l+1}[m-1] + acc_l[m]
+            const int m = x - np + 1;
+            ok[u] = true;
+            dst[u] = W + (l + m - 1) * ld + l;
+            V v = (m <= deg) ? W[(l + m) * ld + l + 1] : zero;
+            if (m >= 2) {
+              const V acc = *dst[u];
+              v.x += acc.x;
+              v.y += acc.y;
+            }
+            a[u] = v;
+            b[u] = hll;
+            c[u] = (m == 1) ? one : ((m - 1 <= deg) ? W[(l + m - 1) * ld + l + 1] : zero);
           }
-        } else {
-          // q_l[m] = q_{l+1}[m] - K_ll q_{l+1}[m-1] + acc_l[m]
-          const int m = w - np + 1;
-          const V Pm = (m <= deg) ? W[(l + m) * ld + l + 1] : zero;
-          const V Pm1 = (m == 1) ? one : ((m - 1 <= deg) ? W[(l + m - 1) * ld + l + 1] : zero);
-          V v = Pm;
-          if (m >= 2) {
-            const V a = W[(l + m - 1) * ld + l];
-            v.x += a.x;
-            v.y += a.y;
-          }
-          cmsub(v, hll, Pm1);
-          W[(l + m - 1) * ld + l] = v;
         }
+#pragma unroll
+        for (int u = 0; u < 2; u++) cmsub(a[u], b[u], c[u]);
+#pragma unroll
+        for (int u = 0; u < 2; u++)
+          if (ok[u]) *dst[u] = a[u];
       }
       V hnext = zero;
       if (l > 0) hnext = W[(l - 1) * ld + l - 1];
@@ -379,101 +496,219 @@ terms_kernel(const typename Cx<R>::t* __restrict__ chat, const TermParams p, dou
       hll = hnext;
     }
 
-    // ---- series: a = d_M, c = d_M - d_K, then Newton, division and exp (Eq. ET_poly) ----
-    for (int m = lt; m <= H + 1; m += G) {
-      V am = zero, bm = zero;
-      if (m == 0) {
-        am = one;
-        bm = one;
-      } else if (m <= Hl) {
-        if (bord) {
-          if (m <= nd - 1) am = W[m * ld + 1];
-          if (m <= nd) bm = W[(m - 1) * ld];
-        } else {
-          if (m <= nd) am = W[(m - 1) * ld];
-          bm = am;
+    if constexpr (STAGE) {
+      // ---- stage a_m = [t^m] d_M (m = 1..h) and c_m = [t^m](d_M - d_K) (m = 1..h+1) ----
+      if (valid) {
+        const long long col = (long long)(t - p.t_begin);
+        const int nc = bord ? 2 * h + 1 : h;
+        for (int x = lt; x < nc; x += G) {
+          const int m = x < h ? x + 1 : x - h + 1;
+          V am = zero, bm = zero;
+          if (m <= Hl) {
+            if (bord) {
+              if (m <= nd - 1) am = W[m * ld + 1];
+              if (m <= nd) bm = W[(m - 1) * ld];
+            } else {
+              if (m <= nd) am = W[(m - 1) * ld];
+            }
+          }
+          stage[(long long)x * stage_ld + col] = (x < h) ? am : cmake<V>(am.x - bm.x, am.y - bm.y);
         }
+        if (lt == 0) wstage[col] = ts->weight;
       }
-      Sa[m] = am;
-      Sc[m] = cmake<V>(am.x - bm.x, am.y - bm.y);
-    }
-    team_sync<G>();
+      team_sync<G>();
+    } else {
+      // ---- series: a = d_M, c = d_M - d_K, then Newton, division and exp (Eq. ET_poly) ----
+      for (int m = lt; m <= H + 1; m += G) {
+        V am = zero, bm = zero;
+        if (m == 0) {
+          am = one;
+          bm = one;
+        } else if (m <= Hl) {
+          if (bord) {
+            if (m <= nd - 1) am = W[m * ld + 1];
+            if (m <= nd) bm = W[(m - 1) * ld];
+          } else {
+            if (m <= nd) am = W[(m - 1) * ld];
+            bm = am;
+          }
+        }
+        Sa[m] = am;
+        Sc[m] = cmake<V>(am.x - bm.x, am.y - bm.y);
+      }
+      team_sync<G>();
 
-    if (G <= 32 || lt < 32) {
-      const int sl = lt;  // < SG
-      if (sl == 0) {
-        SR[0] = zero;
-        SR[1] = Sc[1];
-        Se[0] = one;
-        Sp[0] = zero;
-        Sz[0] = zero;
-      }
-      __syncwarp();
-      for (int k = 1; k <= h; k++) {
-        V sR = zero, sp = zero;
-        for (int i = 1 + sl; i <= k; i += SG) {
-          cmac(sR, Sa[i], SR[k + 1 - i]);
-          if (i < k) cmac(sp, Sa[i], Sp[k - i]);
-        }
-#pragma unroll
-        for (int off = SG / 2; off >= 1; off >>= 1) {
-          sR.x += __shfl_xor_sync(0xffffffffu, sR.x, off);
-          sR.y += __shfl_xor_sync(0xffffffffu, sR.y, off);
-          sp.x += __shfl_xor_sync(0xffffffffu, sp.x, off);
-          sp.y += __shfl_xor_sync(0xffffffffu, sp.y, off);
-        }
-        const V ck = Sc[k + 1], ak = Sa[k];
-        const R kk = (R)k;
-        const V Rk = cmake<V>(ck.x - sR.x, ck.y - sR.y);            // R_{k+1}
-        const V pk = cmake<V>(-rfma(kk, ak.x, sp.x), -rfma(kk, ak.y, sp.y));  // power sum p_k
-        const V zk = cmake<V>((R)0.5 * rfma(kk, Rk.x, pk.x), (R)0.5 * rfma(kk, Rk.y, pk.y));
-        __syncwarp();
+      if (G <= 32 || lt < 32) {
+        const int sl = lt;  // < SG
         if (sl == 0) {
-          SR[k + 1] = Rk;
-          Sp[k] = pk;
-          Sz[k] = zk;
+          SR[0] = zero;
+          SR[1] = Sc[1];
+          Se[0] = one;
+          Sp[0] = zero;
+          Sz[0] = zero;
         }
         __syncwarp();
-        V se = zero;
-        for (int j = 1 + sl; j <= k; j += SG) cmac(se, Sz[j], Se[k - j]);
+        // Step k: R_{k+1}, p_k, z_k = (p_k + k R_{k+1}) / 2 and e_{k-1} = sum_j z_j e_{k-1-j}/(k-1)
+        // from one reduction round (e lags one step, so its dot product needs no z_k).
+        for (int k = 1; k <= h + 1; k++) {
+          const bool rp = k <= h;
+          V sR = zero, sp = zero, se = zero;
+          for (int i = 1 + sl; i <= k; i += SG) {
+            if (rp) cmac(sR, Sa[i], SR[k + 1 - i]);
+            if (i < k) {
+              if (rp) cmac(sp, Sa[i], Sp[k - i]);
+              cmac(se, Sz[i], Se[k - 1 - i]);
+            }
+          }
 #pragma unroll
-        for (int off = SG / 2; off >= 1; off >>= 1) {
-          se.x += __shfl_xor_sync(0xffffffffu, se.x, off);
-          se.y += __shfl_xor_sync(0xffffffffu, se.y, off);
+          for (int off = SG / 2; off >= 1; off >>= 1) {
+            sR.x += __shfl_xor_sync(0xffffffffu, sR.x, off);
+            sR.y += __shfl_xor_sync(0xffffffffu, sR.y, off);
+            sp.x += __shfl_xor_sync(0xffffffffu, sp.x, off);
+            sp.y += __shfl_xor_sync(0xffffffffu, sp.y, off);
+            se.x += __shfl_xor_sync(0xffffffffu, se.x, off);
+            se.y += __shfl_xor_sync(0xffffffffu, se.y, off);
+          }
+          if (sl == 0) {
+            if (rp) {
+              const V ck = Sc[k + 1], ak = Sa[k];
+              const R kk = (R)k;
+              const V Rk = cmake<V>(ck.x - sR.x, ck.y - sR.y);                        // R_{k+1}
+              const V pk = cmake<V>(-rfma(kk, ak.x, sp.x), -rfma(kk, ak.y, sp.y));  // power sum p_k
+              SR[k + 1] = Rk;
+              Sp[k] = pk;
+              Sz[k] = cmake<V>((R)0.5 * rfma(kk, Rk.x, pk.x), (R)0.5 * rfma(kk, Rk.y, pk.y));
+            }
+            if (k >= 2) Se[k - 1] = cmake<V>(se.x * invk[k - 1], se.y * invk[k - 1]);
+          }
+          __syncwarp();
         }
-        if (sl == 0) Se[k] = cmake<V>(se.x * invk[k], se.y * invk[k]);
-        __syncwarp();
-      }
-      if (lt == 0) {
-        const V f = Se[h];
-        const double w = ts->weight;
-        const double fr = (double)f.x * w, fi = (double)f.y * w;
-        if (p.plain) {
-          acc_re += fr;
-          acc_im += fi;
-        } else {
-          dd_add(acc_re, acc_re_lo, fr);
-          dd_add(acc_im, acc_im_lo, fi);
+        if (lt == 0) {
+          const V f = Se[h];
+          const double w = ts->weight;
+          const double fr = (double)f.x * w, fi = (double)f.y * w;
+          if (p.plain) {
+            acc_re += fr;
+            acc_im += fi;
+          } else {
+            dd_add(acc_re, acc_re_lo, fr);
+            dd_add(acc_im, acc_im_lo, fi);
+          }
         }
       }
+      team_sync<G>();
     }
-    team_sync<G>();
   }
 
-  if (lt == 0) {
-    double* o = partials + 4ull * team_global;
-    o[0] = acc_re;
-    o[1] = acc_re_lo;
-    o[2] = acc_im;
-    o[3] = acc_im_lo;
+  if constexpr (!STAGE) {
+    if (lt == 0) {
+      double* o = partials + 4ull * team_global;
+      o[0] = acc_re;
+      o[1] = acc_re_lo;
+      o[2] = acc_im;
+      o[3] = acc_im_lo;
+    }
   }
 }
 
 // ---------------------------------------------------------------------------------------------
-// Double-double reduction of per-team partials, then the exact 2^-h scaling of Eq. fdsieve.
+// Staged series: one term per thread. From a_m = [t^m] d_M and c_m = [t^m](d_M - d_K):
+//   R_{k+1} = c_{k+1} - sum_{i=1..k} a_i R_{k+1-i}           (R = (1 - d_K/d_M)/t, R_1 = c_1)
+//   p_k     = -k a_k - sum_{i=1..k-1} a_i p_{k-i}             (Newton: power sums Tr((C X)^k))
+//   z_k     = k g_k = (p_k + k R_{k+1}) / 2                   (g_k of Eq. ET_poly)
+//   e_k     = (1/k) sum_{j=1..k} z_j e_{k-j},  e_0 = 1,  f = e_h
+// Working arrays live in shared memory, [index][thread]. The weighted values are summed in
+// double-double per block.
+// ---------------------------------------------------------------------------------------------
+constexpr int kSeriesThreads = 64;
+
+template <typename R>
+__global__ void __launch_bounds__(kSeriesThreads)
+series_kernel(const typename Cx<R>::t* __restrict__ stage, const double* __restrict__ wstage, long long count,
+              long long stage_ld, int h, int bord, int plain, double* __restrict__ partials) {
+  using V = typename Cx<R>::t;
+  extern __shared__ __align__(16) unsigned char smem[];
+  V* SR = reinterpret_cast<V*>(smem);             // (h + 2) x threads
+  V* Sp = SR + (size_t)(h + 2) * kSeriesThreads;  // (h + 1) x threads
+  V* Sz = Sp + (size_t)(h + 1) * kSeriesThreads;
+  V* Se = Sz + (size_t)(h + 1) * kSeriesThreads;
+  const int tid = threadIdx.x;
+  const long long tt = (long long)blockIdx.x * kSeriesThreads + tid;
+  const V zero = cmake<V>((R)0, (R)0);
+  double fr = 0.0, fi = 0.0;
+  if (tt < count) {
+    auto A = [&](int m) -> V { return stage[(long long)(m - 1) * stage_ld + tt]; };
+    auto C = [&](int m) -> V { return bord ? stage[(long long)(h + m - 1) * stage_ld + tt] : zero; };
+#define SIDX(i) ((size_t)(i) * kSeriesThreads + tid)
+    SR[SIDX(0)] = zero;
+    SR[SIDX(1)] = C(1);
+    Se[SIDX(0)] = cmake<V>((R)1, (R)0);
+    for (int k = 1; k <= h; k++) {
+      V sR = zero, sp = zero;
+      for (int i = 1; i <= k; i++) {
+        const V ai = A(i);
+        if (bord) cmac(sR, ai, SR[SIDX(k + 1 - i)]);
+        if (i < k) cmac(sp, ai, Sp[SIDX(k - i)]);
+      }
+      const V ck = C(k + 1), ak = A(k);
+      const R kk = (R)k;
+      const V Rk = cmake<V>(ck.x - sR.x, ck.y - sR.y);
+      const V pk = cmake<V>(-rfma(kk, ak.x, sp.x), -rfma(kk, ak.y, sp.y));
+      const V zk = cmake<V>((R)0.5 * rfma(kk, Rk.x, pk.x), (R)0.5 * rfma(kk, Rk.y, pk.y));
+      SR[SIDX(k + 1)] = Rk;
+      Sp[SIDX(k)] = pk;
+      Sz[SIDX(k)] = zk;
+      V se = zero;
+      for (int j = 1; j <= k; j++) cmac(se, Sz[SIDX(j)], Se[SIDX(k - j)]);
+      const R ik = (R)1 / kk;
+      Se[SIDX(k)] = cmake<V>(se.x * ik, se.y * ik);
+    }
+    const V f = Se[SIDX(h)];
+#undef SIDX
+    const double w = wstage[tt];
+    fr = (double)f.x * w;
+    fi = (double)f.y * w;
+  }
+  // block sum in double-double
+  __shared__ double red[4][kSeriesThreads];
+  red[0][tid] = fr;
+  red[1][tid] = 0.0;
+  red[2][tid] = fi;
+  red[3][tid] = 0.0;
+  __syncthreads();
+  for (int off = kSeriesThreads / 2; off >= 1; off >>= 1) {
+    if (tid < off) {
+      double a = red[0][tid], b = red[1][tid], c = red[2][tid], d = red[3][tid];
+      if (plain) {
+        a += red[0][tid + off];
+        c += red[2][tid + off];
+      } else {
+        dd_add_dd(a, b, red[0][tid + off], red[1][tid + off]);
+        dd_add_dd(c, d, red[2][tid + off], red[3][tid + off]);
+      }
+      red[0][tid] = a;
+      red[1][tid] = b;
+      red[2][tid] = c;
+      red[3][tid] = d;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    double* o = partials + 4ll * blockIdx.x;
+    o[0] = red[0][0];
+    o[1] = red[1][0];
+    o[2] = red[2][0];
+    o[3] = red[3][0];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Double-double reduction of partials, then the exact 2^-h scaling of Eq. fdsieve. With
+// accumulate != 0 the sum is added to the dd value already in out_dd (chunked sums).
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-reduce_kernel(const double* __restrict__ partials, long long count, int h, double* out_dd, double2* out_val) {
+reduce_kernel(const double* __restrict__ partials, long long count, int h, double* out_dd, double2* out_val,
+              int accumulate) {
   __shared__ double s[4][256];
   double rh = 0.0, rl = 0.0, ih = 0.0, il = 0.0;
   for (long long i = threadIdx.x; i < count; i += 256) {
@@ -499,19 +734,24 @@ reduce_kernel(const double* __restrict__ partials, long long count, int h, doubl
     __syncthreads();
   }
   if (threadIdx.x == 0) {
+    double a = s[0][0], b = s[1][0], c = s[2][0], d = s[3][0];
+    if (accumulate && out_dd) {
+      dd_add_dd(a, b, out_dd[0], out_dd[1]);
+      dd_add_dd(c, d, out_dd[2], out_dd[3]);
+    }
     if (out_dd) {
-      out_dd[0] = s[0][0];
-      out_dd[1] = s[1][0];
-      out_dd[2] = s[2][0];
-      out_dd[3] = s[3][0];
+      out_dd[0] = a;
+      out_dd[1] = b;
+      out_dd[2] = c;
+      out_dd[3] = d;
     }
     if (out_val) {
       // 2^-h as an exact power of two, applied in up to two steps to stay in range
-      int e1 = h > 1000 ? 1000 : h;
-      int e2 = h - e1;
+      const int e1 = h > 1000 ? 1000 : h;
+      const int e2 = h - e1;
       const double s1 = __longlong_as_double((long long)(1023 - e1) << 52);
       const double s2 = __longlong_as_double((long long)(1023 - e2) << 52);
-      out_val[0] = make_double2((s[0][0] + s[1][0]) * s1 * s2, (s[2][0] + s[3][0]) * s1 * s2);
+      out_val[0] = make_double2((a + b) * s1 * s2, (c + d) * s1 * s2);
     }
   }
 }
@@ -557,11 +797,11 @@ __global__ void gather_kernel(const double2* __restrict__ B, const double2* __re
 int cta_threads(int team) { return cta_of(team); }
 int teams_per_cta(int team) { return cta_of(team) / team; }
 
-size_t team_shared_bytes(bool fp32, int nd, int H, int P) {
+size_t team_shared_bytes(bool fp32, int nd, int H, int P, bool staged) {
   (void)P;
   const size_t cs = fp32 ? sizeof(float2) : sizeof(double2);
   const int ld = nd | 1;
-  size_t b = (size_t)nd * ld * cs + 6 * (size_t)(H + 2) * cs + sizeof(TeamScratch);
+  size_t b = (size_t)nd * ld * cs + (staged ? 0 : 6 * (size_t)(H + 2) * cs) + sizeof(TeamScratch);
   return (b + 15) & ~(size_t)15;
 }
 
@@ -572,35 +812,39 @@ static size_t items_bytes_of(bool fp32, int Hl, int H) {
   return (b + 15) & ~(size_t)15;
 }
 
-size_t cta_shared_bytes(bool fp32, int team, int nd, int H, int Hl, int P) {
-  return items_bytes_of(fp32, Hl, H) + (size_t)teams_per_cta(team) * team_shared_bytes(fp32, nd, H, P);
+size_t cta_shared_bytes(bool fp32, int team, int nd, int H, int Hl, int P, bool staged) {
+  return items_bytes_of(fp32, Hl, H) + (size_t)teams_per_cta(team) * team_shared_bytes(fp32, nd, H, P, staged);
 }
 
-template <typename R, int G> static const void* kernel_ptr() { return (const void*)terms_kernel<R, G>; }
+template <typename R, int G, bool S> static const void* kptr() { return (const void*)terms_kernel<R, G, S>; }
 
-static const void* pick_kernel(bool fp32, int team) {
+template <bool S> static const void* pick_kernel_s(bool fp32, int team) {
   if (fp32) {
     switch (team) {
-      case 8: return kernel_ptr<float, 8>();
-      case 16: return kernel_ptr<float, 16>();
-      case 32: return kernel_ptr<float, 32>();
-      case 64: return kernel_ptr<float, 64>();
-      case 128: return kernel_ptr<float, 128>();
+      case 8: return kptr<float, 8, S>();
+      case 16: return kptr<float, 16, S>();
+      case 32: return kptr<float, 32, S>();
+      case 64: return kptr<float, 64, S>();
+      case 128: return kptr<float, 128, S>();
     }
   } else {
     switch (team) {
-      case 8: return kernel_ptr<double, 8>();
-      case 16: return kernel_ptr<double, 16>();
-      case 32: return kernel_ptr<double, 32>();
-      case 64: return kernel_ptr<double, 64>();
-      case 128: return kernel_ptr<double, 128>();
+      case 8: return kptr<double, 8, S>();
+      case 16: return kptr<double, 16, S>();
+      case 32: return kptr<double, 32, S>();
+      case 64: return kptr<double, 64, S>();
+      case 128: return kptr<double, 128, S>();
     }
   }
   return nullptr;
 }
 
-int max_ctas_per_sm(bool fp32, int team, size_t smem_bytes) {
-  const void* k = pick_kernel(fp32, team);
+static const void* pick_kernel(bool fp32, int team, bool staged) {
+  return staged ? pick_kernel_s<true>(fp32, team) : pick_kernel_s<false>(fp32, team);
+}
+
+int max_ctas_per_sm(bool fp32, int team, size_t smem_bytes, bool staged) {
+  const void* k = pick_kernel(fp32, team, staged);
   if (!k) return 0;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess) return 0;
   int n = 0;
@@ -609,19 +853,39 @@ int max_ctas_per_sm(bool fp32, int team, size_t smem_bytes) {
 }
 
 cudaError_t launch_terms(bool fp32, int team, const void* chat, const TermParams& p, int grid, double* partials,
-                         cudaStream_t stream) {
-  const void* k = pick_kernel(fp32, team);
+                         cudaStream_t stream, void* stage, double* wstage, long long stage_ld) {
+  const bool staged = stage != nullptr;
+  const void* k = pick_kernel(fp32, team, staged);
   if (!k) return cudaErrorInvalidValue;
   const size_t smem = (size_t)p.items_bytes + (size_t)teams_per_cta(team) * p.team_bytes;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  void* args[] = {(void*)&chat, (void*)&p, (void*)&partials};
+  void* args[] = {(void*)&chat, (void*)&p, (void*)&partials, (void*)&stage, (void*)&wstage, (void*)&stage_ld};
   return cudaLaunchKernel(k, dim3(grid), dim3(cta_of(team)), args, smem, stream);
 }
 
+size_t series_shared_bytes(bool fp32, int h) {
+  const size_t cs = fp32 ? sizeof(float2) : sizeof(double2);
+  return (size_t)(4 * h + 5) * kSeriesThreads * cs;
+}
+
+long long series_blocks(long long count) { return (count + kSeriesThreads - 1) / kSeriesThreads; }
+
+cudaError_t launch_series(bool fp32, const void* stage, const double* wstage, long long count, long long stage_ld,
+                          int h, int bord, int plain, double* partials, cudaStream_t stream) {
+  const size_t smem = series_shared_bytes(fp32, h);
+  const void* k = fp32 ? (const void*)series_kernel<float> : (const void*)series_kernel<double>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long blocks = series_blocks(count);
+  void* args[] = {(void*)&stage, (void*)&wstage, (void*)&count, (void*)&stage_ld, (void*)&h,
+                  (void*)&bord,  (void*)&plain,  (void*)&partials};
+  return cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(kSeriesThreads), args, smem, stream);
+}
+
 cudaError_t launch_reduce(const double* partials, long long count, int h, double* out_dd, double2* out_val,
-                          cudaStream_t stream) {
-  reduce_kernel<<<1, 256, 0, stream>>>(partials, count, h, out_dd, out_val);
+                          cudaStream_t stream, int accumulate) {
+  reduce_kernel<<<1, 256, 0, stream>>>(partials, count, h, out_dd, out_val, accumulate);
   return cudaGetLastError();
 }
 
