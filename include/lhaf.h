@@ -63,6 +63,7 @@ typedef enum {
                                         explicit duplicated-row matrix, 2^(N/2) terms */
 #define LHAF_NO_LOOPS 0x10u          /* declare gamma == 0 on the occupied modes (skips the loop
                                         border); with host pointers this is detected by itself */
+#define LHAF_BATCH_B_PER_ITEM 0x20u  /* lhaf_batched: B holds one M x M matrix per item */
 
 /* Compiled limits. */
 #define LHAF_MAX_DIM 64      /* working dimension n_dim = 2 * pairs (+1 loop border) */
@@ -118,6 +119,21 @@ lhaf_status lhaf_range(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128
  * degree h and loop border flag `bordered` (8 per complex multiply-add of the elimination
  * Hessenberg reduction, La Budde's recurrence and the series recurrences). 0 for invalid sizes. */
 double lhaf_flops_per_term(int n_dim, int h, int bordered);
+
+/* Batched loop hafnians (the batch of conditional probabilities of one chain-rule step, App. A.2,
+ * and the batching motivation of App. B.5): item i is lhaf(B_n) with pattern reps[i*M .. i*M+M-1].
+ *   B      : one M x M matrix shared by all items, or batch x M x M with LHAF_BATCH_B_PER_ITEM.
+ *   gamma  : batch x M loop weights (item i at gamma + i*M), or NULL for diag(B).
+ *   reps   : HOST, batch x M.
+ *   out    : batch lhaf_c128 (host, or device with LHAF_DEVICE_PTRS, like B and gamma).
+ *   item_status : HOST, batch entries, or NULL: per-item LHAF_OK / LHAF_EINVAL / LHAF_ETOOBIG; a
+ *            failed item's out is NaN and does not fail the call.
+ *   stats  : terms = all sieve terms, n_dim / h = the largest, pairs = work units, team = lanes
+ *            per term, kernel_ms = device time of the persistent launch and the reduction.
+ * All items run in one persistent kernel over a queue of term ranges ordered longest first. */
+lhaf_status lhaf_batched(lhaf_ctx* ctx, int batch, int M, const lhaf_c128* B, const lhaf_c128* gamma,
+                         const int32_t* reps, uint32_t flags, lhaf_c128* out, lhaf_status* item_status,
+                         lhaf_stats* stats);
 
 /* Host-side double-double sum of `count` partials (4 doubles each, as from lhaf_range) scaled
  * by 2^-h (exact). */

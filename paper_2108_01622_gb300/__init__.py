@@ -25,6 +25,7 @@ FP32_TERMS = 0x2
 PLAIN_ACCUM = 0x4
 NO_REPEAT_SPEEDUP = 0x8
 NO_LOOPS = 0x10
+BATCH_B_PER_ITEM = 0x20
 
 STATUS = {0: "LHAF_OK", 1: "LHAF_EINVAL", 2: "LHAF_ETOOBIG", 3: "LHAF_ECUDA", 4: "LHAF_ETIMEOUT",
           5: "LHAF_ENOMEM", 6: "LHAF_ECANCELLED"}
@@ -73,6 +74,8 @@ def _lib():
         L.lhaf_combine.restype = c.c_int
         L.lhaf_flops_per_term.argtypes = [c.c_int, c.c_int, c.c_int]
         L.lhaf_flops_per_term.restype = c.c_double
+        L.lhaf_batched.argtypes = [vp, c.c_int, c.c_int, vp, vp, vp, c.c_uint32, vp, vp, ctypes.POINTER(Stats)]
+        L.lhaf_batched.restype = c.c_int
         L.lhaf_fp64_probe.argtypes = [c.c_int, ctypes.POINTER(c.c_double)]
         L.lhaf_fp64_probe.restype = c.c_int
         _LIB = L
@@ -234,3 +237,37 @@ class Context:
             _check(self._lib.lhaf_range(self._h, M, _ptr(B), _ptr(gamma), _ptr(r), flags, term_begin, term_end,
                                         part.ctypes.data, ctypes.byref(st) if stats else None), "lhaf_range")
         return (part, st.as_dict()) if stats else part
+
+    def lhaf_batched(self, B, gammas, reps, flags: int = 0, stats: bool = False, out=None):
+        """Loop hafnians of a batch: item i uses reps[i] and gammas[i] (batch x M; None for diag(B))
+        with the shared M x M matrix B (or batch x M x M with BATCH_B_PER_ITEM). Host inputs return
+        (values, item_status) as numpy arrays; torch CUDA inputs write `out` (complex128, batch)."""
+        dev = _is_torch(B) and B.is_cuda
+        r = np.ascontiguousarray(np.asarray(reps, dtype=np.int32))
+        if r.ndim != 2:
+            raise ValueError("reps must be batch x M")
+        batch, M = r.shape
+        st = Stats()
+        status = np.zeros(batch, dtype=np.int32)
+        if dev:
+            import torch
+
+            flags |= DEVICE_PTRS
+            B = B.to(torch.complex128).contiguous()
+            g = None if gammas is None else gammas.to(torch.complex128).contiguous()
+            if out is None:
+                out = torch.empty(batch, dtype=torch.complex128, device=B.device)
+            _check(self._lib.lhaf_batched(self._h, batch, M, B.data_ptr(), None if g is None else g.data_ptr(),
+                                          r.ctypes.data, flags, out.data_ptr(), status.ctypes.data,
+                                          ctypes.byref(st) if stats else None), "lhaf_batched")
+            res = out
+        else:
+            Bh = _host_c128(B)
+            gh = None if gammas is None else _host_c128(gammas)
+            res = np.zeros(batch, np.complex128)
+            _check(self._lib.lhaf_batched(self._h, batch, M, Bh.ctypes.data, None if gh is None else gh.ctypes.data,
+                                          r.ctypes.data, flags, res.ctypes.data, status.ctypes.data,
+                                          ctypes.byref(st) if stats else None), "lhaf_batched")
+        if stats:
+            return res, status, st.as_dict()
+        return res, status

@@ -15,30 +15,9 @@
 #include "../../include/lhaf.h"
 #include "lhaf_internal.h"
 #include "lhaf_plan.h"
+#include "lhaf_ctx.h"
 
 using namespace lhafgpu;
-
-struct lhaf_ctx {
-  int device = 0;
-  int sms = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  // device workspace
-  double2* d_chat = nullptr;
-  float2* d_chat32 = nullptr;
-  double* d_partials = nullptr;
-  size_t partial_cap = 0;  // teams
-  double* d_out = nullptr;  // 4 dd doubles + 2 value doubles
-  void* d_stage = nullptr;  // staged characteristic polynomials (series_kernel input)
-  double* d_wstage = nullptr;
-  size_t stage_bytes = 0, wstage_terms = 0;
-  // pinned host staging
-  double2* h_chat = nullptr;
-  float2* h_chat32 = nullptr;
-  double* h_out = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  std::mutex mu;
-};
 
 extern "C" const char* lhaf_strerror(lhaf_status s) {
   switch (s) {
@@ -70,6 +49,14 @@ extern "C" void lhaf_ctx_destroy(lhaf_ctx* ctx) {
   cudaFreeHost(ctx->h_out);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  if (ctx->tev0) cudaEventDestroy(ctx->tev0);
+  if (ctx->tev1) cudaEventDestroy(ctx->tev1);
+  for (DevBuf* b : {&ctx->b_items, &ctx->b_units, &ctx->b_queue, &ctx->b_next, &ctx->b_partials, &ctx->b_unit_begin,
+                    &ctx->b_item_h, &ctx->b_chat, &ctx->b_chat32, &ctx->b_out, &ctx->b_B, &ctx->b_gamma})
+    b->release();
+  for (HostBuf* b : {&ctx->hb_items, &ctx->hb_units, &ctx->hb_queue, &ctx->hb_unit_begin, &ctx->hb_item_h,
+                     &ctx->hb_chat, &ctx->hb_chat32, &ctx->hb_out})
+    b->release();
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   cudaSetDevice(prev);
   delete ctx;
@@ -106,7 +93,8 @@ extern "C" lhaf_status lhaf_ctx_create(lhaf_ctx** out, int device, void* cuda_st
             cudaMallocHost(&c->h_chat, nchat * sizeof(double2)) == cudaSuccess &&
             cudaMallocHost(&c->h_chat32, nchat * sizeof(float2)) == cudaSuccess &&
             cudaMallocHost(&c->h_out, 8 * sizeof(double)) == cudaSuccess &&
-            cudaEventCreate(&c->ev0) == cudaSuccess && cudaEventCreate(&c->ev1) == cudaSuccess;
+            cudaEventCreate(&c->ev0) == cudaSuccess && cudaEventCreate(&c->ev1) == cudaSuccess &&
+            cudaEventCreate(&c->tev0) == cudaSuccess && cudaEventCreate(&c->tev1) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     lhaf_ctx_destroy(c);
@@ -144,35 +132,129 @@ namespace {
 
 bool finite_c(const lhaf_c128& z) { return std::isfinite(z.re) && std::isfinite(z.im); }
 
-// Choose the lanes-per-term team size: a model of FP64 lane utilisation times the share of the
-// four SM sub-partitions that hold at least one warp. LHAF_TEAM in the environment overrides.
-int choose_team(lhaf_ctx* ctx, bool fp32, const Plan& pl, bool staged, int* ctas_per_sm) {
+}  // namespace
+
+namespace lhafgpu {
+
+void fill_params(const Plan& pl, bool fp32, bool staged, int team, uint32_t flags, TermParams& p) {
+  std::memset(&p, 0, sizeof(p));
+  p.nd = pl.nd;
+  p.ld = pl.nd | 1;
+  p.bord = pl.bord;
+  p.h = pl.h;
+  p.H = pl.H;
+  p.Hl = pl.Hl;
+  p.P = pl.P;
+  p.hp = pl.hp;
+  p.hp_even = pl.hp_even;
+  p.plain = (flags & LHAF_PLAIN_ACCUM) ? 1 : 0;
+  p.n_items = pl.Hl * (pl.Hl - 1) / 2;
+  p.team_bytes = (int)team_shared_bytes(fp32, pl.nd, pl.H, pl.P, staged);
+  p.items_bytes = (int)(cta_shared_bytes(fp32, team, pl.nd, pl.H, pl.Hl, pl.P, staged) -
+                        (size_t)teams_per_cta(team) * p.team_bytes);
+  for (int q = 0; q < pl.P; q++) {
+    p.eta[q] = pl.eta[q];
+    p.radix[q] = pl.radix[q];
+  }
+}
+
+// Team size (lanes per term). LHAF_TEAM forces one. Otherwise each candidate that fits in shared
+// memory runs a short slice of real terms (two rounds of the resident grid), timed with CUDA
+// events; the fastest per term is cached for the problem shape. Problems too small to time
+// meaningfully use a model of FP64 lane utilisation times sub-partition coverage instead.
+int pick_team(lhaf_ctx* ctx, bool fp32, const Plan& pl, bool staged, int family, const void* chat,
+              int* ctas_per_sm) {
   const char* env = std::getenv("LHAF_TEAM");
-  int forced = env ? std::atoi(env) : 0;
+  const int forced = env ? std::atoi(env) : 0;
   const int cands[5] = {8, 16, 32, 64, 128};
-  double best = -1.0;
-  int best_g = 32, best_occ = 0;
-  for (int g : cands) {
+  int occs[5] = {0, 0, 0, 0, 0};
+  double model_best = -1.0;
+  int model_g = 0;
+  for (int c = 0; c < 5; c++) {
+    const int g = cands[c];
     if (forced && g != forced) continue;
     const size_t smem = cta_shared_bytes(fp32, g, pl.nd, pl.H, pl.Hl, pl.P, staged);
     if (smem > 227 * 1024) continue;
-    const int occ = max_ctas_per_sm(fp32, g, smem, staged);
-    if (occ <= 0) continue;
-    const double warps = (double)occ * cta_threads(g) / 32.0;
-    const double cover = std::min(1.0, warps / 4.0);
-    const double eff = model_lane_efficiency(pl.nd, pl.Hl, pl.h, pl.bord, g);
-    const double score = eff * cover * (warps >= 8.0 ? 1.0 : 0.9);
-    if (score > best) {
-      best = score;
-      best_g = g;
-      best_occ = occ;
+    occs[c] = max_ctas_per_sm(fp32, g, smem, staged);
+    if (occs[c] <= 0) continue;
+    const double warps = (double)occs[c] * cta_threads(g) / 32.0;
+    const double score = model_lane_efficiency(pl.nd, pl.Hl, pl.h, pl.bord, g) * std::min(1.0, warps / 4.0) *
+                         (warps >= 8.0 ? 1.0 : 0.9);
+    if (score > model_best) {
+      model_best = score;
+      model_g = g;
     }
   }
-  if (best < 0) return 0;
-  (void)ctx;
-  *ctas_per_sm = best_occ;
+  if (model_g == 0) return 0;
+  auto occ_of = [&](int g) {
+    for (int c = 0; c < 5; c++)
+      if (cands[c] == g) return occs[c];
+    return 0;
+  };
+  if (forced) {
+    *ctas_per_sm = occ_of(forced);
+    return forced;
+  }
+  const TuneKey key{fp32 ? 1 : 0, staged ? 1 : 0, pl.nd, pl.Hl, pl.h, pl.bord, family};
+  auto it = ctx->tuned.find(key);
+  if (it != ctx->tuned.end()) {
+    *ctas_per_sm = occ_of(it->second);
+    return it->second;
+  }
+  const char* env_tune = std::getenv("LHAF_AUTOTUNE");
+  const bool tune = !(env_tune && env_tune[0] == '0');
+  int best_g = model_g;
+  if (tune && chat) {
+    double best_per_term = 1e300;
+    for (int c = 0; c < 5; c++) {
+      const int g = cands[c];
+      if (occs[c] <= 0) continue;
+      TermParams p;
+      fill_params(pl, fp32, staged, g, 0, p);
+      const uint64_t grid = (uint64_t)ctx->sms * (uint64_t)occs[c];
+      p.total_teams = grid * (uint64_t)teams_per_cta(g);
+      if (p.total_teams > ctx->partial_cap) continue;
+      const uint64_t S = std::min<uint64_t>(pl.T, 2 * p.total_teams);
+      if (S < p.total_teams) {  // fewer terms than teams: too small to tell apart, use the model
+        best_g = model_g;
+        best_per_term = -1.0;
+        break;
+      }
+      p.rounds = (S + p.total_teams - 1) / p.total_teams;
+      p.t_begin = 0;
+      p.t_end = S;
+      void* stage = staged ? ctx->d_stage : nullptr;
+      const long long stage_ld = staged ? (long long)ctx->wstage_terms : 0;
+      if (staged && (uint64_t)stage_ld < S) continue;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; rep++) {
+        cudaEventRecord(ctx->tev0, ctx->stream);
+        if (launch_terms(fp32, g, chat, p, (int)grid, ctx->d_partials, ctx->stream, stage, ctx->d_wstage, stage_ld) !=
+            cudaSuccess) {
+          cudaGetLastError();
+          ms = -1.f;
+          break;
+        }
+        cudaEventRecord(ctx->tev1, ctx->stream);
+        cudaEventSynchronize(ctx->tev1);
+        cudaEventElapsedTime(&ms, ctx->tev0, ctx->tev1);
+      }
+      if (ms <= 0.f) continue;
+      const double per_term = ms / (double)S;
+      if (per_term < best_per_term) {
+        best_per_term = per_term;
+        best_g = g;
+      }
+    }
+  }
+  ctx->tuned[key] = best_g;
+  *ctas_per_sm = occ_of(best_g);
   return best_g;
 }
+
+}  // namespace lhafgpu
+
+namespace {
 
 // Build the slot matrix into ctx->d_chat (and d_chat32 for FP32 terms).
 lhaf_status stage_chat(lhaf_ctx* ctx, const Plan& pl, int M, const lhaf_c128* B, const lhaf_c128* gamma,
@@ -267,33 +349,15 @@ lhaf_status run_terms(lhaf_ctx* ctx, const Plan& pl, uint32_t flags, uint64_t tb
     if (!staged) chunk = T;
   }
   int occ = 0;
-  const int team = choose_team(ctx, fp32, pl, staged, &occ);
+  const void* chat = fp32 ? (const void*)ctx->d_chat32 : (const void*)ctx->d_chat;
+  const int team = pick_team(ctx, fp32, pl, staged, 0, chat, &occ);
   if (team == 0) return LHAF_ETOOBIG;
   TermParams p;
-  std::memset(&p, 0, sizeof(p));
-  p.nd = pl.nd;
-  p.ld = pl.nd | 1;
-  p.bord = pl.bord;
-  p.h = pl.h;
-  p.H = pl.H;
-  p.Hl = pl.Hl;
-  p.P = pl.P;
-  p.hp = pl.hp;
-  p.hp_even = pl.hp_even;
-  p.plain = (flags & LHAF_PLAIN_ACCUM) ? 1 : 0;
-  p.n_items = pl.Hl * (pl.Hl - 1) / 2;
-  p.team_bytes = (int)team_shared_bytes(fp32, pl.nd, pl.H, pl.P, staged);
-  p.items_bytes = (int)(cta_shared_bytes(fp32, team, pl.nd, pl.H, pl.Hl, pl.P, staged) -
-                        (size_t)teams_per_cta(team) * p.team_bytes);
-  for (int q = 0; q < pl.P; q++) {
-    p.eta[q] = pl.eta[q];
-    p.radix[q] = pl.radix[q];
-  }
+  fill_params(pl, fp32, staged, team, flags, p);
   const int tpc = teams_per_cta(team);
   const uint64_t max_ctas = (uint64_t)ctx->sms * (uint64_t)occ;
   double* acc_dd = dd_dst ? dd_dst : ctx->d_out;  // running double-double sum over chunks
   if (timed) cudaEventRecord(ctx->ev0, ctx->stream);
-  const void* chat = fp32 ? (const void*)ctx->d_chat32 : (const void*)ctx->d_chat;
   uint64_t c0 = tb;
   int ci = 0;
   do {

@@ -32,6 +32,18 @@ struct TermParams {
   unsigned long long total_teams;
 };
 
+// Batched form: one item (loop hafnian) and one work unit (a term range of one item).
+struct BatchItem {
+  TermParams p;         // the item's sieve (t_begin/t_end/rounds/total_teams set per unit)
+  long long chat_off;   // element offset of the item's slot matrix in the pool
+  int slot_mode[kMaxDim];
+};
+struct BatchUnit {
+  int item;
+  int pad;
+  unsigned long long t0, t1;
+};
+
 // Launch the FP64 (fp32 = false) or FP32 term kernel. chat is the bordered slot matrix (nd x nd,
 // row-major) in double2 (fp32 = false) or float2. Without `stage` every team finishes its terms
 // and writes 4 doubles (its double-double partial) to partials. With `stage`, each term's
@@ -61,6 +73,20 @@ cudaError_t launch_series(bool fp32, const void* stage, const double* wstage, lo
 // output may be NULL.
 cudaError_t launch_reduce(const double* partials, long long count, int h, double* out_dd,
                           double2* out_val, cudaStream_t stream, int accumulate = 0);
+
+// Batched persistent kernel and its helpers.
+size_t cta_table_bytes(bool fp32, int Hl, int H);
+int batched_ctas_per_sm(bool fp32, int team, size_t smem_bytes);
+cudaError_t launch_batched(bool fp32, int team, const void* chat_pool, const BatchItem* items,
+                           const BatchUnit* units, const int* queue, int n_units, int* next_unit,
+                           double* unit_partials, int team_bytes, int items_bytes, int grid,
+                           cudaStream_t stream);
+cudaError_t launch_batch_reduce(const double* unit_partials, const int* item_unit_begin,
+                                const int* item_h, int teams, int n_items, double2* out,
+                                cudaStream_t stream);
+cudaError_t launch_batch_gather(const double2* B, long long B_stride, const double2* gamma,
+                                long long gamma_stride, int M, const BatchItem* items, int n_items,
+                                double2* chat_pool, float2* chat32_pool, cudaStream_t stream);
 
 // Gather the bordered slot matrix from device B (M x M, upper triangle read) and gamma.
 // slot_mode: modes of the 2P slots (-1 = pad). gamma may be NULL (diag(B) is used).

@@ -158,23 +158,43 @@ struct TeamScratch {  // small per-team area
 };
 
 // ---------------------------------------------------------------------------------------------
-// The sieve terms. STAGE: write d_M and d_M - d_K per term to `stage` (coefficient-major,
-// stage_ld terms per row) and the weight to `wstage`, instead of finishing the term here.
+// CTA tables shared by the teams: the push items (d, e) of La Budde's recurrence sorted by e then
+// d (2 <= d, d + e <= Hl), and 1/k for k <= H + 1.
+// ---------------------------------------------------------------------------------------------
+template <typename R, int CTA>
+__device__ __forceinline__ void build_cta_tables(const TermParams& p, unsigned char* smem) {
+  uint16_t* items = reinterpret_cast<uint16_t*>(smem);
+  R* invk = reinterpret_cast<R*>(smem + ((p.n_items * 2 + 15) & ~15));
+  const int Hl = p.Hl;
+  for (int w = threadIdx.x; w < p.n_items; w += CTA) {
+    int e = 0, base = 0;
+    while (base + (Hl - 1 - e) <= w) {
+      base += Hl - 1 - e;
+      e++;
+    }
+    items[w] = (uint16_t)(((2 + (w - base)) << 8) | e);
+  }
+  for (int k = threadIdx.x; k <= p.H + 1; k += CTA) invk[k] = k ? (R)1 / (R)k : (R)0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// The sieve terms t = p.t_begin + team_global + r * p.total_teams (r < p.rounds, t < p.t_end)
+// of one loop hafnian, for the team of the calling thread. acc (lane 0 of the team) receives the
+// double-double sum (re_hi, re_lo, im_hi, im_lo) of weight * f. STAGE: instead of finishing a
+// term, write d_M and d_M - d_K to `stage` (coefficient-major, stage_ld terms per row, column
+// t - p.t_begin) and its weight to `wstage`.
 // ---------------------------------------------------------------------------------------------
 template <typename R, int G, bool STAGE>
-__global__ void __launch_bounds__(cta_of(G))
-terms_kernel(const typename Cx<R>::t* __restrict__ chat, const TermParams p, double* __restrict__ partials,
-             typename Cx<R>::t* __restrict__ stage, double* __restrict__ wstage, long long stage_ld) {
+__device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict__ chat, const TermParams& p,
+                                            unsigned char* smem, unsigned long long team_global,
+                                            typename Cx<R>::t* __restrict__ stage, double* __restrict__ wstage,
+                                            long long stage_ld, double* acc) {
   using V = typename Cx<R>::t;
-  constexpr int CTA = cta_of(G);
-  constexpr int TEAMS = CTA / G;
   constexpr int SG = G < 32 ? G : 32;  // lanes of the first warp of a team
-  extern __shared__ __align__(16) unsigned char smem[];
 
   const int nd = p.nd, ld = p.ld, bord = p.bord, h = p.h, H = p.H, Hl = p.Hl, P = p.P;
-  const int tid = threadIdx.x;
-  const int team = tid / G;
-  const int lt = tid - team * G;
+  const int team = threadIdx.x / G;
+  const int lt = threadIdx.x - team * G;
 
   uint16_t* items = reinterpret_cast<uint16_t*>(smem);
   R* invk = reinterpret_cast<R*>(smem + ((p.n_items * 2 + 15) & ~15));
@@ -188,21 +208,8 @@ terms_kernel(const typename Cx<R>::t* __restrict__ chat, const TermParams p, dou
   V* Se = Sz + (H + 2);
   TeamScratch* ts = reinterpret_cast<TeamScratch*>(STAGE ? (void*)(W + nd * ld) : (void*)(Se + (H + 2)));
 
-  // Push items (d, e) of La Budde's recurrence, sorted by e then d: 2 <= d, d + e <= Hl.
-  for (int w = tid; w < p.n_items; w += CTA) {
-    int e = 0, base = 0;
-    while (base + (Hl - 1 - e) <= w) {
-      base += Hl - 1 - e;
-      e++;
-    }
-    items[w] = (uint16_t)(((2 + (w - base)) << 8) | e);
-  }
-  for (int k = tid; k <= H + 1; k += CTA) invk[k] = k ? (R)1 / (R)k : (R)0;
-  __syncthreads();
-
   const V zero = cmake<V>((R)0, (R)0);
   const V one = cmake<V>((R)1, (R)0);
-  const unsigned long long team_global = (unsigned long long)blockIdx.x * TEAMS + team;
   double acc_re = 0.0, acc_re_lo = 0.0, acc_im = 0.0, acc_im_lo = 0.0;
 
   for (unsigned long long rnd = 0; rnd < p.rounds; rnd++) {
@@ -600,14 +607,152 @@ terms_kernel(const typename Cx<R>::t* __restrict__ chat, const TermParams p, dou
     }
   }
 
+  acc[0] = acc_re;
+  acc[1] = acc_re_lo;
+  acc[2] = acc_im;
+  acc[3] = acc_im_lo;
+}
+
+// One loop hafnian over a grid of CTAs: team tg of the grid takes terms tg, tg + teams, ...
+template <typename R, int G, bool STAGE>
+__global__ void __launch_bounds__(cta_of(G))
+terms_kernel(const typename Cx<R>::t* __restrict__ chat, const __grid_constant__ TermParams p,
+             double* __restrict__ partials, typename Cx<R>::t* __restrict__ stage, double* __restrict__ wstage,
+             long long stage_ld) {
+  constexpr int CTA = cta_of(G);
+  constexpr int TEAMS = CTA / G;
+  extern __shared__ __align__(16) unsigned char smem[];
+  build_cta_tables<R, CTA>(p, smem);
+  __syncthreads();
+  const int team = threadIdx.x / G;
+  const int lt = threadIdx.x - team * G;
+  const unsigned long long team_global = (unsigned long long)blockIdx.x * TEAMS + team;
+  double acc[4];
+  sieve_terms<R, G, STAGE>(chat, p, smem, team_global, stage, wstage, stage_ld, acc);
   if constexpr (!STAGE) {
     if (lt == 0) {
       double* o = partials + 4ull * team_global;
-      o[0] = acc_re;
-      o[1] = acc_re_lo;
-      o[2] = acc_im;
-      o[3] = acc_im_lo;
+      o[0] = acc[0];
+      o[1] = acc[1];
+      o[2] = acc[2];
+      o[3] = acc[3];
     }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batched loop hafnians: a persistent grid pops work units (item, term range) from a queue ordered
+// longest first; all teams of a CTA work on the unit's item (same working dimension, so the
+// teams of a warp stay in step). Each team writes one double-double partial per unit.
+// ---------------------------------------------------------------------------------------------
+template <typename R, int G>
+__global__ void __launch_bounds__(cta_of(G))
+batched_kernel(const typename Cx<R>::t* __restrict__ chat_pool, const BatchItem* __restrict__ items,
+               const BatchUnit* __restrict__ units, const int* __restrict__ queue, int n_units,
+               int* __restrict__ next_unit, double* __restrict__ unit_partials, int team_bytes,
+               int items_bytes) {
+  constexpr int CTA = cta_of(G);
+  constexpr int TEAMS = CTA / G;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ TermParams sp;
+  __shared__ int s_q;
+  __shared__ long long s_off;
+  const int team = threadIdx.x / G;
+  const int lt = threadIdx.x - team * G;
+  for (;;) {
+    if (threadIdx.x == 0) s_q = atomicAdd(next_unit, 1);
+    __syncthreads();
+    const int q = s_q;
+    if (q >= n_units) break;
+    const int u = queue[q];
+    if (threadIdx.x == 0) {
+      const BatchUnit un = units[u];
+      sp = items[un.item].p;
+      s_off = items[un.item].chat_off;
+      sp.t_begin = un.t0;
+      sp.t_end = un.t1;
+      sp.total_teams = TEAMS;
+      sp.rounds = (un.t1 - un.t0 + TEAMS - 1) / TEAMS;
+      sp.team_bytes = team_bytes;
+      sp.items_bytes = items_bytes;
+    }
+    __syncthreads();
+    build_cta_tables<R, CTA>(sp, smem);
+    __syncthreads();
+    double acc[4];
+    sieve_terms<R, G, false>(chat_pool + s_off, sp, smem, (unsigned long long)team, nullptr, nullptr, 0, acc);
+    if (lt == 0) {
+      double* o = unit_partials + 4ll * ((long long)u * TEAMS + team);
+      o[0] = acc[0];
+      o[1] = acc[1];
+      o[2] = acc[2];
+      o[3] = acc[3];
+    }
+    __syncthreads();
+  }
+}
+
+// One warp per item: double-double sum of its units' team partials, then 2^-h (Eq. fdsieve).
+// h < 0 marks an empty pattern (lhaf = 1); h == INT_MAX marks an item that was not computed.
+__global__ void __launch_bounds__(128)
+batch_reduce_kernel(const double* __restrict__ unit_partials, const int* __restrict__ item_unit_begin,
+                    const int* __restrict__ item_h, int teams, int n_items, double2* __restrict__ out) {
+  const int item = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (item >= n_items) return;
+  const long long b = (long long)item_unit_begin[item] * teams, e = (long long)item_unit_begin[item + 1] * teams;
+  double rh = 0.0, rl = 0.0, ih = 0.0, il = 0.0;
+  for (long long i = b + lane; i < e; i += 32) {
+    dd_add_dd(rh, rl, unit_partials[4 * i + 0], unit_partials[4 * i + 1]);
+    dd_add_dd(ih, il, unit_partials[4 * i + 2], unit_partials[4 * i + 3]);
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const double a = __shfl_xor_sync(0xffffffffu, rh, off), bb = __shfl_xor_sync(0xffffffffu, rl, off);
+    const double c = __shfl_xor_sync(0xffffffffu, ih, off), d = __shfl_xor_sync(0xffffffffu, il, off);
+    dd_add_dd(rh, rl, a, bb);
+    dd_add_dd(ih, il, c, d);
+  }
+  if (lane == 0) {
+    const int h = item_h[item];
+    if (h < 0) {
+      out[item] = make_double2(1.0, 0.0);
+    } else if (h == 0x7fffffff) {
+      out[item] = make_double2(__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll));
+    } else {
+      const double s1 = __longlong_as_double((long long)(1023 - h) << 52);
+      out[item] = make_double2((rh + rl) * s1, (ih + il) * s1);
+    }
+  }
+}
+
+// One block per item: the item's bordered slot matrix from device B (shared M x M, or one per
+// item at B_stride) and gamma (M per item at gamma_stride; NULL: diag of B).
+__global__ void batch_gather_kernel(const double2* __restrict__ B, long long B_stride, const double2* __restrict__ gamma,
+                                    long long gamma_stride, int M, const BatchItem* __restrict__ items,
+                                    double2* __restrict__ chat_pool, float2* __restrict__ chat32_pool) {
+  const int item = blockIdx.x;
+  const BatchItem& it = items[item];
+  const int nd = it.p.nd, bord = it.p.bord;
+  if (nd <= 0) return;
+  const double2* Bi = B + (long long)item * B_stride;
+  const double2* gi = gamma ? gamma + (long long)item * gamma_stride : nullptr;
+  for (int w = threadIdx.x; w < nd * nd; w += blockDim.x) {
+    const int i = w / nd, j = w - i * nd;
+    double2 c = make_double2(0.0, 0.0);
+    if (bord && i == 0 && j == 0) {
+    } else if (bord && (i == 0 || j == 0)) {
+      const int m = it.slot_mode[(i == 0 ? j : i) - 1];
+      c = (m < 0) ? make_double2(1.0, 0.0) : (gi ? gi[m] : Bi[(size_t)m * M + m]);
+    } else {
+      const int a = it.slot_mode[i - bord], bm = it.slot_mode[j - bord];
+      if (a >= 0 && bm >= 0) {
+        const int lo = a < bm ? a : bm, hi = a < bm ? bm : a;
+        c = Bi[(size_t)lo * M + hi];
+      }
+    }
+    if (chat_pool) chat_pool[it.chat_off + w] = c;
+    if (chat32_pool) chat32_pool[it.chat_off + w] = make_float2((float)c.x, (float)c.y);
   }
 }
 
@@ -881,6 +1026,59 @@ cudaError_t launch_series(bool fp32, const void* stage, const double* wstage, lo
   void* args[] = {(void*)&stage, (void*)&wstage, (void*)&count, (void*)&stage_ld, (void*)&h,
                   (void*)&bord,  (void*)&plain,  (void*)&partials};
   return cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(kSeriesThreads), args, smem, stream);
+}
+
+size_t cta_table_bytes(bool fp32, int Hl, int H) { return items_bytes_of(fp32, Hl, H); }
+
+template <typename R, int G> static const void* bptr() { return (const void*)batched_kernel<R, G>; }
+
+static const void* pick_batched(bool fp32, int team) {
+  switch (team) {
+    case 8: return fp32 ? bptr<float, 8>() : bptr<double, 8>();
+    case 16: return fp32 ? bptr<float, 16>() : bptr<double, 16>();
+    case 32: return fp32 ? bptr<float, 32>() : bptr<double, 32>();
+    case 64: return fp32 ? bptr<float, 64>() : bptr<double, 64>();
+    case 128: return fp32 ? bptr<float, 128>() : bptr<double, 128>();
+  }
+  return nullptr;
+}
+
+int batched_ctas_per_sm(bool fp32, int team, size_t smem_bytes) {
+  const void* k = pick_batched(fp32, team);
+  if (!k) return 0;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, cta_of(team), smem_bytes) != cudaSuccess) return 0;
+  return n;
+}
+
+cudaError_t launch_batched(bool fp32, int team, const void* chat_pool, const BatchItem* items, const BatchUnit* units,
+                           const int* queue, int n_units, int* next_unit, double* unit_partials, int team_bytes,
+                           int items_bytes, int grid, cudaStream_t stream) {
+  const void* k = pick_batched(fp32, team);
+  if (!k) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)items_bytes + (size_t)teams_per_cta(team) * team_bytes;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&chat_pool, (void*)&items,     (void*)&units,     (void*)&queue,      (void*)&n_units,
+                  (void*)&next_unit, (void*)&unit_partials, (void*)&team_bytes, (void*)&items_bytes};
+  return cudaLaunchKernel(k, dim3(grid), dim3(cta_of(team)), args, smem, stream);
+}
+
+cudaError_t launch_batch_reduce(const double* unit_partials, const int* item_unit_begin, const int* item_h, int teams,
+                                int n_items, double2* out, cudaStream_t stream) {
+  if (n_items <= 0) return cudaSuccess;
+  batch_reduce_kernel<<<(n_items + 3) / 4, 128, 0, stream>>>(unit_partials, item_unit_begin, item_h, teams, n_items,
+                                                             out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_gather(const double2* B, long long B_stride, const double2* gamma, long long gamma_stride,
+                                int M, const BatchItem* items, int n_items, double2* chat_pool, float2* chat32_pool,
+                                cudaStream_t stream) {
+  if (n_items <= 0) return cudaSuccess;
+  batch_gather_kernel<<<n_items, 256, 0, stream>>>(B, B_stride, gamma, gamma_stride, M, items, chat_pool, chat32_pool);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const double* partials, long long count, int h, double* out_dd, double2* out_val,
