@@ -7,6 +7,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <vector>
@@ -80,11 +81,14 @@ extern "C" lhaf_status lhaf_batched(lhaf_ctx* ctx, int batch, int M, const lhaf_
   }
   if (item_status)
     for (int i = 0; i < batch; i++) item_status[i] = st[i];
+  // items with sieve terms to evaluate (valid plan, N > 0)
+  std::vector<char> runnable(batch, 0);
+  for (int i = 0; i < batch; i++) runnable[i] = (st[i] == LHAF_OK && plans[i].N > 0) ? 1 : 0;
 
   // ---- per-item descriptors, slot-matrix pool, costs ----
   std::vector<int> work;  // items with terms
   for (int i = 0; i < batch; i++)
-    if (item_h[i] > 0) work.push_back(i);
+    if (runnable[i]) work.push_back(i);
   if (!ctx->hb_items.reserve(sizeof(BatchItem) * batch) || !ctx->b_items.reserve(sizeof(BatchItem) * batch) ||
       !ctx->hb_item_h.reserve(sizeof(int) * batch) || !ctx->b_item_h.reserve(sizeof(int) * batch) ||
       !ctx->hb_unit_begin.reserve(sizeof(int) * (batch + 1)) || !ctx->b_unit_begin.reserve(sizeof(int) * (batch + 1)) ||
@@ -97,7 +101,7 @@ extern "C" lhaf_status lhaf_batched(lhaf_ctx* ctx, int batch, int M, const lhaf_
   std::vector<double> fpt(batch, 0.0);
   for (int i = 0; i < batch; i++) {
     std::memset(&hitems[i], 0, sizeof(BatchItem));
-    if (item_h[i] <= 0) continue;
+    if (!runnable[i]) continue;
     const Plan& pl = plans[i];
     fill_params(pl, fp32, false, 32, flags, hitems[i].p);
     hitems[i].chat_off = pool;
@@ -147,6 +151,20 @@ extern "C" lhaf_status lhaf_batched(lhaf_ctx* ctx, int batch, int M, const lhaf_
     }
   }
 
+  // Items of degree <= kStageMaxDegree stage their term polynomials and finish them one term per
+  // thread (series_units_kernel); larger degrees finish each term in the team (inline).
+  const char* env_stage = std::getenv("LHAF_STAGE");
+  const bool stage_ok = !(env_stage && env_stage[0] == '0');
+  bool any_inline = false;
+  int h_max_staged = 0;
+  for (int i : work) {
+    if (stage_ok && plans[i].h <= kStageMaxDegree) {
+      h_max_staged = std::max(h_max_staged, plans[i].h);
+    } else {
+      any_inline = true;
+    }
+  }
+
   // ---- team size: tuned on the costliest item, shared-memory layout for the largest ----
   int team = 16, occ = 0;
   const void* chat_pool = fp32 ? ctx->b_chat32.p : ctx->b_chat.p;
@@ -154,16 +172,23 @@ extern "C" lhaf_status lhaf_batched(lhaf_ctx* ctx, int batch, int M, const lhaf_
   if (rep >= 0) {
     const char* chatp = static_cast<const char*>(chat_pool) + (size_t)hitems[rep].chat_off * (fp32 ? 8 : 16);
     int occ_rep = 0;
-    // the single-term kernel reads its slot matrix from ctx->d_chat; tune against the pool copy
+    // tuned with the single-lhaf kernel on the costliest item's slot matrix (in the pool)
     team = pick_team(ctx, fp32, plans[rep], false, 1, chatp, &occ_rep);
+    (void)occ_rep;
     if (team == 0) team = 32;
-    Plan big = plans[rep];
-    big.nd = nd_max;
-    big.H = H_max;
-    big.Hl = Hl_max;
-    team_bytes = team_shared_bytes(fp32, nd_max, H_max, 0, false);
+    team_bytes = team_shared_bytes(fp32, nd_max, H_max, 0, any_inline ? false : true);
     items_bytes = cta_table_bytes(fp32, Hl_max, H_max);
-    while (items_bytes + (size_t)teams_per_cta(team) * team_bytes > 227 * 1024 && team < 128) team *= 2;
+    // the fused series reuses the team area: (4h + 5) entries per CTA thread
+    const size_t series_bytes = (size_t)(4 * h_max_staged + 5) * cta_threads(team) * (fp32 ? 8 : 16);
+    if (h_max_staged > 0 && (size_t)teams_per_cta(team) * team_bytes < series_bytes)
+      team_bytes = ((series_bytes + teams_per_cta(team) - 1) / teams_per_cta(team) + 15) & ~(size_t)15;
+    while (items_bytes + (size_t)teams_per_cta(team) * team_bytes > 227 * 1024 && team < 128) {
+      team *= 2;
+      const size_t sb = (size_t)(4 * h_max_staged + 5) * cta_threads(team) * (fp32 ? 8 : 16);
+      team_bytes = team_shared_bytes(fp32, nd_max, H_max, 0, any_inline ? false : true);
+      if (h_max_staged > 0 && (size_t)teams_per_cta(team) * team_bytes < sb)
+        team_bytes = ((sb + teams_per_cta(team) - 1) / teams_per_cta(team) + 15) & ~(size_t)15;
+    }
     occ = batched_ctas_per_sm(fp32, team, items_bytes + (size_t)teams_per_cta(team) * team_bytes);
     if (occ <= 0) return LHAF_ETOOBIG;
   }
@@ -177,9 +202,10 @@ extern "C" lhaf_status lhaf_batched(lhaf_ctx* ctx, int batch, int M, const lhaf_
   const double target = cost_total / (double)(n_ctas * 8);
   for (int i = 0; i < batch; i++) {
     unit_begin[i] = (int)units.size();
-    if (item_h[i] <= 0) continue;
+    if (!runnable[i]) continue;
     const uint64_t T = plans[i].T;
     uint64_t ut = (uint64_t)std::ceil(target / std::max(fpt[i], 1.0));
+    ut = std::min<uint64_t>(ut, 4096);  // bounds the per-CTA staging region
     ut = std::max<uint64_t>(ut, (uint64_t)TEAMS);
     ut = ((ut + TEAMS - 1) / TEAMS) * TEAMS;
     for (uint64_t t0 = 0; t0 < T; t0 += ut) {
@@ -188,6 +214,8 @@ extern "C" lhaf_status lhaf_batched(lhaf_ctx* ctx, int batch, int M, const lhaf_
       u.pad = 0;
       u.t0 = t0;
       u.t1 = std::min<uint64_t>(T, t0 + ut);
+      u.stage_off = -1;
+      u.w_off = 0;
       units.push_back(u);
       ucost.push_back(fpt[i] * (double)(u.t1 - u.t0));
     }
@@ -197,6 +225,28 @@ extern "C" lhaf_status lhaf_batched(lhaf_ctx* ctx, int batch, int M, const lhaf_
   std::vector<int> queue(n_units);
   std::iota(queue.begin(), queue.end(), 0);
   std::stable_sort(queue.begin(), queue.end(), [&](int a, int b) { return ucost[a] > ucost[b]; });
+
+  // Staged units: each CTA stages the polynomials of the unit it runs in a private region of
+  // region_elems entries (the largest staged unit) and finishes them itself.
+  const size_t cs_b = fp32 ? sizeof(float2) : sizeof(double2);
+  const long long grid_b = std::min<long long>(n_ctas, std::max(n_units, 1));
+  long long region_elems = 0, w_region = 0;
+  for (const BatchUnit& u : units) {
+    const Plan& pl = plans[u.item];
+    if (!(stage_ok && pl.h <= kStageMaxDegree)) continue;
+    const long long rows = pl.bord ? 2 * (long long)pl.h + 1 : (long long)pl.h;
+    region_elems = std::max(region_elems, rows * (long long)(u.t1 - u.t0));
+    w_region = std::max(w_region, (long long)(u.t1 - u.t0));
+  }
+  for (BatchUnit& u : units) {
+    const Plan& pl = plans[u.item];
+    const bool staged_u = stage_ok && pl.h <= kStageMaxDegree;
+    u.stage_off = staged_u ? region_elems : -1;
+    u.w_off = staged_u ? w_region : 0;
+  }
+  if (region_elems > 0 && (!ctx->b_stage.reserve((size_t)region_elems * grid_b * cs_b) ||
+                           !ctx->b_wstage.reserve((size_t)w_region * grid_b * sizeof(double))))
+    return LHAF_ENOMEM;
 
   if (!ctx->hb_units.reserve(sizeof(BatchUnit) * std::max(n_units, 1)) ||
       !ctx->b_units.reserve(sizeof(BatchUnit) * std::max(n_units, 1)) ||
@@ -237,10 +287,10 @@ extern "C" lhaf_status lhaf_batched(lhaf_ctx* ctx, int batch, int M, const lhaf_
   if (!ok) return LHAF_ECUDA;
   if (stats) cudaEventRecord(ctx->ev0, s);
   if (n_units > 0) {
-    const int grid = (int)std::min<long long>(n_ctas, n_units);
     if (launch_batched(fp32, team, chat_pool, (const BatchItem*)ctx->b_items.p, (const BatchUnit*)ctx->b_units.p,
                        (const int*)ctx->b_queue.p, n_units, (int*)ctx->b_next.p, (double*)ctx->b_partials.p,
-                       (int)team_bytes, (int)items_bytes, grid, s) != cudaSuccess)
+                       (int)team_bytes, (int)items_bytes, (int)grid_b, s, region_elems ? ctx->b_stage.p : nullptr,
+                       region_elems ? (double*)ctx->b_wstage.p : nullptr) != cudaSuccess)
       return LHAF_ECUDA;
   }
   double2* dout = dev ? (double2*)out : (double2*)ctx->b_out.p;

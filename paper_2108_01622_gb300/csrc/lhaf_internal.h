@@ -42,6 +42,8 @@ struct BatchUnit {
   int item;
   int pad;
   unsigned long long t0, t1;
+  long long stage_off;  // staged unit: entries of the per-CTA staging region; -1: inline unit
+  long long w_off;      // staged unit: entries of the per-CTA weight region
 };
 
 // Launch the FP64 (fp32 = false) or FP32 term kernel. chat is the bordered slot matrix (nd x nd,
@@ -80,7 +82,7 @@ int batched_ctas_per_sm(bool fp32, int team, size_t smem_bytes);
 cudaError_t launch_batched(bool fp32, int team, const void* chat_pool, const BatchItem* items,
                            const BatchUnit* units, const int* queue, int n_units, int* next_unit,
                            double* unit_partials, int team_bytes, int items_bytes, int grid,
-                           cudaStream_t stream);
+                           cudaStream_t stream, void* stage = nullptr, double* wstage = nullptr);
 cudaError_t launch_batch_reduce(const double* unit_partials, const int* item_unit_begin,
                                 const int* item_h, int teams, int n_items, double2* out,
                                 cudaStream_t stream);

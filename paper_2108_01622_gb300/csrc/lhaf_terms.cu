@@ -640,6 +640,64 @@ terms_kernel(const typename Cx<R>::t* __restrict__ chat, const __grid_constant__
   }
 }
 
+constexpr int kSeriesThreadsB = 64;
+
+// Series of n staged terms (coefficient-major, ld terms per row), NT threads, one term per thread
+// per round; working arrays in `smem` ([index][thread], (4h + 5) x NT entries). Returns this
+// thread's double-double sum of weight * f in acc (re_hi, re_lo, im_hi, im_lo).
+template <typename R, int NT>
+__device__ __forceinline__ void series_range(const typename Cx<R>::t* __restrict__ st, long long ld,
+                                             const double* __restrict__ ws, long long n, int h, int bord,
+                                             unsigned char* smem, int tid, double* acc) {
+  using V = typename Cx<R>::t;
+  V* SR = reinterpret_cast<V*>(smem);
+  V* Sp = SR + (size_t)(h + 2) * NT;
+  V* Sz = Sp + (size_t)(h + 1) * NT;
+  V* Se = Sz + (size_t)(h + 1) * NT;
+  const V zero = cmake<V>((R)0, (R)0);
+  double rh = 0.0, rl = 0.0, ih = 0.0, il = 0.0;
+  for (long long base = 0; base < n; base += NT) {
+    const long long tt = base + tid;
+    if (tt < n) {
+      auto A = [&](int m) -> V { return st[(long long)(m - 1) * ld + tt]; };
+      auto C = [&](int m) -> V { return bord ? st[(long long)(h + m - 1) * ld + tt] : zero; };
+#define SIDX(i) ((size_t)(i) * NT + tid)
+      SR[SIDX(0)] = zero;
+      SR[SIDX(1)] = C(1);
+      Se[SIDX(0)] = cmake<V>((R)1, (R)0);
+      for (int k = 1; k <= h; k++) {
+        V sR = zero, sp = zero;
+        for (int i = 1; i <= k; i++) {
+          const V ai = A(i);
+          if (bord) cmac(sR, ai, SR[SIDX(k + 1 - i)]);
+          if (i < k) cmac(sp, ai, Sp[SIDX(k - i)]);
+        }
+        const V ck = C(k + 1), ak = A(k);
+        const R kk = (R)k;
+        const V Rk = cmake<V>(ck.x - sR.x, ck.y - sR.y);
+        const V pk = cmake<V>(-rfma(kk, ak.x, sp.x), -rfma(kk, ak.y, sp.y));
+        const V zk = cmake<V>((R)0.5 * rfma(kk, Rk.x, pk.x), (R)0.5 * rfma(kk, Rk.y, pk.y));
+        SR[SIDX(k + 1)] = Rk;
+        Sp[SIDX(k)] = pk;
+        Sz[SIDX(k)] = zk;
+        V se = zero;
+        for (int j = 1; j <= k; j++) cmac(se, Sz[SIDX(j)], Se[SIDX(k - j)]);
+        const R ik = (R)1 / kk;
+        Se[SIDX(k)] = cmake<V>(se.x * ik, se.y * ik);
+      }
+      const V f = Se[SIDX(h)];
+#undef SIDX
+      const double w = ws[tt];
+      dd_add(rh, rl, (double)f.x * w);
+      dd_add(ih, il, (double)f.y * w);
+    }
+  }
+  acc[0] = rh;
+  acc[1] = rl;
+  acc[2] = ih;
+  acc[3] = il;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Batched loop hafnians: a persistent grid pops work units (item, term range) from a queue ordered
 // longest first; all teams of a CTA work on the unit's item (same working dimension, so the
@@ -650,13 +708,14 @@ __global__ void __launch_bounds__(cta_of(G))
 batched_kernel(const typename Cx<R>::t* __restrict__ chat_pool, const BatchItem* __restrict__ items,
                const BatchUnit* __restrict__ units, const int* __restrict__ queue, int n_units,
                int* __restrict__ next_unit, double* __restrict__ unit_partials, int team_bytes,
-               int items_bytes) {
+               int items_bytes, typename Cx<R>::t* __restrict__ stage, double* __restrict__ wstage) {
   constexpr int CTA = cta_of(G);
   constexpr int TEAMS = CTA / G;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TermParams sp;
   __shared__ int s_q;
-  __shared__ long long s_off;
+  __shared__ long long s_off, s_stage, s_w;
+  __shared__ int s_staged;
   const int team = threadIdx.x / G;
   const int lt = threadIdx.x - team * G;
   for (;;) {
@@ -669,6 +728,9 @@ batched_kernel(const typename Cx<R>::t* __restrict__ chat_pool, const BatchItem*
       const BatchUnit un = units[u];
       sp = items[un.item].p;
       s_off = items[un.item].chat_off;
+      s_stage = un.stage_off;  // per-CTA region size (elements), or -1 for an inline unit
+      s_w = un.w_off;          // per-CTA weight region size
+      s_staged = (stage != nullptr && un.stage_off >= 0) ? 1 : 0;
       sp.t_begin = un.t0;
       sp.t_end = un.t1;
       sp.total_teams = TEAMS;
@@ -680,13 +742,45 @@ batched_kernel(const typename Cx<R>::t* __restrict__ chat_pool, const BatchItem*
     build_cta_tables<R, CTA>(sp, smem);
     __syncthreads();
     double acc[4];
-    sieve_terms<R, G, false>(chat_pool + s_off, sp, smem, (unsigned long long)team, nullptr, nullptr, 0, acc);
-    if (lt == 0) {
-      double* o = unit_partials + 4ll * ((long long)u * TEAMS + team);
-      o[0] = acc[0];
-      o[1] = acc[1];
-      o[2] = acc[2];
-      o[3] = acc[3];
+    if (s_staged) {
+      // The unit's polynomials go to this CTA's staging region; then the CTA's threads finish them
+      // one term per thread (working arrays over the team area of shared memory) and the CTA's
+      // double-double sum becomes the unit's partial (first team slot; the others are zeroed).
+      const long long n = (long long)(sp.t_end - sp.t_begin);
+      typename Cx<R>::t* cst = stage + s_stage * (long long)blockIdx.x;
+      double* cw = wstage + s_w * (long long)blockIdx.x;
+      sieve_terms<R, G, true>(chat_pool + s_off, sp, smem, (unsigned long long)team, cst, cw, n, acc);
+      __syncthreads();
+      series_range<R, CTA>(cst, n, cw, n, sp.h, sp.bord, smem + items_bytes, threadIdx.x, acc);
+      __shared__ double red[4][CTA];
+      red[0][threadIdx.x] = acc[0];
+      red[1][threadIdx.x] = acc[1];
+      red[2][threadIdx.x] = acc[2];
+      red[3][threadIdx.x] = acc[3];
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
+        for (int x = 0; x < CTA; x++) {
+          dd_add_dd(a, b, red[0][x], red[1][x]);
+          dd_add_dd(c, d, red[2][x], red[3][x]);
+        }
+        for (int tm = 0; tm < TEAMS; tm++) {
+          double* o = unit_partials + 4ll * ((long long)u * TEAMS + tm);
+          o[0] = tm == 0 ? a : 0.0;
+          o[1] = tm == 0 ? b : 0.0;
+          o[2] = tm == 0 ? c : 0.0;
+          o[3] = tm == 0 ? d : 0.0;
+        }
+      }
+    } else {
+      sieve_terms<R, G, false>(chat_pool + s_off, sp, smem, (unsigned long long)team, nullptr, nullptr, 0, acc);
+      if (lt == 0) {
+        double* o = unit_partials + 4ll * ((long long)u * TEAMS + team);
+        o[0] = acc[0];
+        o[1] = acc[1];
+        o[2] = acc[2];
+        o[3] = acc[3];
+      }
     }
     __syncthreads();
   }
@@ -1054,14 +1148,15 @@ int batched_ctas_per_sm(bool fp32, int team, size_t smem_bytes) {
 
 cudaError_t launch_batched(bool fp32, int team, const void* chat_pool, const BatchItem* items, const BatchUnit* units,
                            const int* queue, int n_units, int* next_unit, double* unit_partials, int team_bytes,
-                           int items_bytes, int grid, cudaStream_t stream) {
+                           int items_bytes, int grid, cudaStream_t stream, void* stage, double* wstage) {
   const void* k = pick_batched(fp32, team);
   if (!k) return cudaErrorInvalidValue;
   const size_t smem = (size_t)items_bytes + (size_t)teams_per_cta(team) * team_bytes;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  void* args[] = {(void*)&chat_pool, (void*)&items,     (void*)&units,     (void*)&queue,      (void*)&n_units,
-                  (void*)&next_unit, (void*)&unit_partials, (void*)&team_bytes, (void*)&items_bytes};
+  void* args[] = {(void*)&chat_pool,     (void*)&items,      (void*)&units,       (void*)&queue,
+                  (void*)&n_units,       (void*)&next_unit,  (void*)&unit_partials, (void*)&team_bytes,
+                  (void*)&items_bytes,   (void*)&stage,      (void*)&wstage};
   return cudaLaunchKernel(k, dim3(grid), dim3(cta_of(team)), args, smem, stream);
 }
 

@@ -72,7 +72,7 @@ def test_chain_rule_batch_sample_matches_single_calls(ctx, lg):
     assert np.all(status == 0)
     for i in range(len(R)):
         single = ctx.lhaf(b.B, G[i], R[i])
-        assert rel(vals[i], single) < 1e-11, i
+        assert rel(vals[i], single) < TOL, i
     # oracle on the smaller items
     small = [i for i in range(len(R)) if R[i].sum() <= 18][:12]
     for i in small:
