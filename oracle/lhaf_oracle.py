@@ -89,19 +89,20 @@ def et_poly_coefficient(g: np.ndarray, h: int) -> np.ndarray:
     Polynomial powers are formed literally, truncated at degree h.
     """
     T = g.shape[0]
+    dt = g.dtype
     if h == 0:
-        return np.ones(T, dtype=complex)
-    base = np.zeros((T, h + 1), dtype=complex)
+        return np.ones(T, dtype=dt)
+    base = np.zeros((T, h + 1), dtype=dt)
     base[:, 1:] = g[:, :h]
-    power = np.zeros((T, h + 1), dtype=complex)
+    power = np.zeros((T, h + 1), dtype=dt)
     power[:, 0] = 1.0
-    total = np.zeros(T, dtype=complex)
+    total = np.zeros(T, dtype=dt)
     for j in range(1, h + 1):
         new = np.zeros_like(power)
         for d in range(h + 1):  # truncated product power * base
             new[:, d] = np.sum(power[:, : d + 1] * base[:, d::-1], axis=1)
         power = new
-        total = total + power[:, h] / math.factorial(j)
+        total = total + power[:, h] / dt.type(math.factorial(j))
     return total
 
 
@@ -109,24 +110,25 @@ def _g_coefficients(C: np.ndarray, v: np.ndarray, Xs: np.ndarray, h: int) -> np.
     """g_k = Tr((C X)^k)/(2k) + v X (C X)^(k-1) v^T / 2, k = 1..h (Eq. ET_poly), for a batch of
     pairing matrices Xs (T, n, n). Powers by repeated matrix products."""
     T, n, _ = Xs.shape
-    g = np.zeros((T, h), dtype=complex)
+    dt = np.result_type(C.dtype, Xs.dtype)
+    g = np.zeros((T, h), dtype=dt)
     if n == 0:
         return g
     CX = np.matmul(C[None, :, :], Xs)  # (T, n, n)
-    P = np.broadcast_to(np.eye(n, dtype=complex), (T, n, n)).copy()  # (C X)^(k-1)
+    P = np.broadcast_to(np.eye(n, dtype=dt), (T, n, n)).copy()  # (C X)^(k-1)
     vX = np.matmul(v[None, None, :], Xs)[:, 0, :]  # (T, n)
     for k in range(1, h + 1):
         loop = np.einsum("ti,tij,j->t", vX, P, v)
         P = np.matmul(P, CX)  # now (C X)^k
         tr = np.einsum("tii->t", P)
-        g[:, k - 1] = tr / (2 * k) + loop / 2
+        g[:, k - 1] = tr / dt.type(2 * k) + loop / dt.type(2)
     return g
 
 
-def _pairing_matrices(deltas: np.ndarray) -> np.ndarray:
+def _pairing_matrices(deltas: np.ndarray, dtype=np.complex128) -> np.ndarray:
     """X_delta = [[0, diag(delta)], [diag(delta), 0]] for each row of deltas (App. B.4)."""
     T, H = deltas.shape
-    X = np.zeros((T, 2 * H, 2 * H), dtype=complex)
+    X = np.zeros((T, 2 * H, 2 * H), dtype=dtype)
     ar = np.arange(H)
     X[:, ar, H + ar] = deltas
     X[:, H + ar, ar] = deltas
@@ -302,11 +304,14 @@ def reduced_slot_problem(B, gamma, reps):
 
 
 def repeated_sieve_terms(B, gamma, reps, start: int = 0, stop: Optional[int] = None,
-                         batch: int = 2048) -> List[complex]:
+                         batch: int = 2048, dtype=np.complex128) -> list:
     """The signed, weighted sieve terms prod_i C(eta_i,k_i) (-1)^(k_i) f(C X_delta') for the digit
     vectors k number start..stop-1 in itertools.product order (App. B.2, B.4). Used by
-    lhaf_repeated (all terms) and by timing on a bounded sample of terms."""
+    lhaf_repeated (all terms) and by timing on a bounded sample of terms. dtype: complex128 (the
+    paper's precision) or np.clongdouble for an extended-precision reference of the same sum."""
     C, v, etas, h = reduced_slot_problem(B, gamma, reps)
+    C = C.astype(dtype)
+    v = v.astype(dtype)
     total = math.prod(e + 1 for e in etas)
     stop = total if stop is None else min(stop, total)
     digit_ranges = [range(e + 1) for e in etas]
@@ -322,14 +327,14 @@ def repeated_sieve_terms(B, gamma, reps, start: int = 0, stop: Optional[int] = N
                 for row in ks
             ],
             dtype=float,
-        )
-        g = _g_coefficients(C, v, _pairing_matrices(deltas), h)
+        ).astype(dtype)
+        g = _g_coefficients(C, v, _pairing_matrices(deltas, dtype), h)
         f = et_poly_coefficient(g, h)
-        terms.extend((weights * f).tolist())
+        terms.extend(list(weights * f))
     return terms
 
 
-def lhaf_repeated(B, gamma, reps, batch: int = 2048) -> complex:
+def lhaf_repeated(B, gamma, reps, batch: int = 2048, dtype=np.complex128):
     """lhaf(A_n) by the finite difference sieve over greedy repeated pairs (App. B.2, B.4).
 
     For pair i repeated eta_i times, k_i in 0..eta_i copies carry -1, so
@@ -342,7 +347,13 @@ def lhaf_repeated(B, gamma, reps, batch: int = 2048) -> complex:
     if N == 0:
         return 1.0 + 0j
     h = (N + 1) // 2
-    return _fsum_complex(repeated_sieve_terms(B, gamma, reps, batch=batch)) / 2.0**h
+    terms = repeated_sieve_terms(B, gamma, reps, batch=batch, dtype=dtype)
+    if np.dtype(dtype) == np.complex128:
+        return _fsum_complex(terms) / 2.0**h
+    # extended precision: sum in that precision, smallest magnitudes first
+    arr = np.array(terms, dtype=dtype)
+    arr = arr[np.argsort(np.abs(arr))]
+    return np.sum(arr) / dtype(2) ** h
 
 
 # ---------------------------------------------------------------------------------------------
