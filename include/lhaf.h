@@ -135,6 +135,18 @@ lhaf_status lhaf_batched(lhaf_ctx* ctx, int batch, int M, const lhaf_c128* B, co
                          const int32_t* reps, uint32_t flags, lhaf_c128* out, lhaf_status* item_status,
                          lhaf_stats* stats);
 
+/* GBS pattern probability of a pure Gaussian state (App. A, Eq. mixed_prob with the pure-state
+ * block form Eq. Adef): squeezed vacuum in every mode (a -> a cosh r - a^dag sinh r), then the
+ * interferometer a -> U a, then the displacement alpha. On the host: the complex covariance
+ * sigma = S S^dag / 2, sigma_Q = sigma + I/2, B = first block of A = X (I - sigma_Q^-1),
+ * gamma = first M entries of alpha_full^dag sigma_Q^-1, P0 = exp(-alpha_full^dag sigma_Q^-1
+ * alpha_full / 2) / sqrt(det sigma_Q); on the GPU: lhaf(B_n). Result P = P0 |lhaf|^2 / prod n_i!.
+ *   U: HOST M x M row-major; r: HOST M squeezing parameters; alpha: HOST M (NULL = no displacement);
+ *   n: HOST M photon counts; prob: HOST double; lhaf_B: HOST, optional (the loop hafnian).
+ * flags: LHAF_FP32_TERMS / LHAF_PLAIN_ACCUM / LHAF_NO_REPEAT_SPEEDUP as for lhaf(). */
+lhaf_status gbs_pattern_prob(lhaf_ctx* ctx, int M, const lhaf_c128* U, const double* r, const lhaf_c128* alpha,
+                             const int32_t* n, uint32_t flags, double* prob, lhaf_c128* lhaf_B);
+
 /* Host-side double-double sum of `count` partials (4 doubles each, as from lhaf_range) scaled
  * by 2^-h (exact). */
 lhaf_status lhaf_combine(int count, const double* partials_dd, int32_t h, lhaf_c128* out);

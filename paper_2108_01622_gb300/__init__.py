@@ -76,6 +76,8 @@ def _lib():
         L.lhaf_flops_per_term.restype = c.c_double
         L.lhaf_batched.argtypes = [vp, c.c_int, c.c_int, vp, vp, vp, c.c_uint32, vp, vp, ctypes.POINTER(Stats)]
         L.lhaf_batched.restype = c.c_int
+        L.gbs_pattern_prob.argtypes = [vp, c.c_int, vp, vp, vp, vp, c.c_uint32, ctypes.POINTER(c.c_double), vp]
+        L.gbs_pattern_prob.restype = c.c_int
         L.lhaf_fp64_probe.argtypes = [c.c_int, ctypes.POINTER(c.c_double)]
         L.lhaf_fp64_probe.restype = c.c_int
         _LIB = L
@@ -271,3 +273,17 @@ class Context:
         if stats:
             return res, status, st.as_dict()
         return res, status
+
+    def gbs_pattern_prob(self, U, r, alpha, n, flags: int = 0):
+        """(P(n), lhaf(B_n)) for the pure state (U, r, alpha) (App. A, Eq. mixed_prob)."""
+        Uh = _host_c128(U)
+        M = Uh.shape[0]
+        rh = np.ascontiguousarray(np.asarray(r, dtype=np.float64))
+        ah = None if alpha is None else _host_c128(alpha)
+        nh = _reps_arr(n, M)
+        prob = ctypes.c_double()
+        lh = np.zeros(1, np.complex128)
+        _check(self._lib.gbs_pattern_prob(self._h, M, Uh.ctypes.data, rh.ctypes.data,
+                                          None if ah is None else ah.ctypes.data, nh.ctypes.data, flags,
+                                          ctypes.byref(prob), lh.ctypes.data), "gbs_pattern_prob")
+        return prob.value, complex(lh[0])

@@ -1,0 +1,140 @@
+// GBS pattern probability of a pure Gaussian state (arXiv:2108.01622, App. A, Eq. mixed_prob with
+// the pure-state block form Eq. Adef): host linear algebra for the kernel matrix, then one loop
+// hafnian on the GPU.
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "../../include/lhaf.h"
+
+namespace {
+
+using cd = std::complex<double>;
+
+// In-place LU with partial pivoting of an n x n row-major matrix; returns false if singular.
+// log|det| and the sign/phase of det are accumulated.
+bool lu_factor(std::vector<cd>& a, int n, std::vector<int>& piv, cd& det_phase, double& log_abs_det) {
+  piv.resize(n);
+  det_phase = 1.0;
+  log_abs_det = 0.0;
+  for (int k = 0; k < n; k++) {
+    int p = k;
+    double best = std::abs(a[(size_t)k * n + k]);
+    for (int i = k + 1; i < n; i++) {
+      const double v = std::abs(a[(size_t)i * n + k]);
+      if (v > best) {
+        best = v;
+        p = i;
+      }
+    }
+    if (best == 0.0) return false;
+    piv[k] = p;
+    if (p != k) {
+      for (int j = 0; j < n; j++) std::swap(a[(size_t)k * n + j], a[(size_t)p * n + j]);
+      det_phase = -det_phase;
+    }
+    const cd d = a[(size_t)k * n + k];
+    log_abs_det += std::log(std::abs(d));
+    det_phase *= d / std::abs(d);
+    for (int i = k + 1; i < n; i++) {
+      const cd l = a[(size_t)i * n + k] / d;
+      a[(size_t)i * n + k] = l;
+      for (int j = k + 1; j < n; j++) a[(size_t)i * n + j] -= l * a[(size_t)k * n + j];
+    }
+  }
+  return true;
+}
+
+// Inverse from an LU factorisation (column by column).
+void lu_inverse(const std::vector<cd>& lu, int n, const std::vector<int>& piv, std::vector<cd>& inv) {
+  inv.assign((size_t)n * n, 0.0);
+  std::vector<cd> x(n);
+  for (int c = 0; c < n; c++) {
+    for (int i = 0; i < n; i++) x[i] = (i == c) ? 1.0 : 0.0;
+    for (int k = 0; k < n; k++)
+      if (piv[k] != k) std::swap(x[k], x[piv[k]]);
+    for (int i = 0; i < n; i++)
+      for (int j = 0; j < i; j++) x[i] -= lu[(size_t)i * n + j] * x[j];
+    for (int i = n - 1; i >= 0; i--) {
+      for (int j = i + 1; j < n; j++) x[i] -= lu[(size_t)i * n + j] * x[j];
+      x[i] /= lu[(size_t)i * n + i];
+    }
+    for (int i = 0; i < n; i++) inv[(size_t)i * n + c] = x[i];
+  }
+}
+
+}  // namespace
+
+extern "C" lhaf_status gbs_pattern_prob(lhaf_ctx* ctx, int M, const lhaf_c128* U, const double* r,
+                                        const lhaf_c128* alpha, const int32_t* n, uint32_t flags, double* prob,
+                                        lhaf_c128* lhaf_B) {
+  if (!ctx || M <= 0 || !U || !r || !n || !prob) return LHAF_EINVAL;
+  if (flags & LHAF_DEVICE_PTRS) return LHAF_EINVAL;  // host inputs only
+  for (int i = 0; i < M; i++) {
+    if (n[i] < 0 || !std::isfinite(r[i])) return LHAF_EINVAL;
+    if (alpha && !(std::isfinite(alpha[i].re) && std::isfinite(alpha[i].im))) return LHAF_EINVAL;
+    for (int j = 0; j < M; j++)
+      if (!(std::isfinite(U[(size_t)i * M + j].re) && std::isfinite(U[(size_t)i * M + j].im))) return LHAF_EINVAL;
+  }
+  const int M2 = 2 * M;
+  // S = [[U, 0], [0, U*]] [[cosh r, -sinh r], [-sinh r, cosh r]]  (a -> a cosh r - a^dag sinh r, then U)
+  std::vector<cd> S((size_t)M2 * M2, 0.0);
+  for (int i = 0; i < M; i++)
+    for (int j = 0; j < M; j++) {
+      const cd u(U[(size_t)i * M + j].re, U[(size_t)i * M + j].im);
+      const double ch = std::cosh(r[j]), sh = std::sinh(r[j]);
+      S[(size_t)i * M2 + j] = u * ch;
+      S[(size_t)i * M2 + (M + j)] = -u * sh;
+      S[(size_t)(M + i) * M2 + j] = -std::conj(u) * sh;
+      S[(size_t)(M + i) * M2 + (M + j)] = std::conj(u) * ch;
+    }
+  // sigma_Q = sigma + I/2 with sigma = S S^dag / 2  (App. A: complex covariance of the Q-function)
+  std::vector<cd> sQ((size_t)M2 * M2, 0.0);
+  for (int i = 0; i < M2; i++)
+    for (int j = 0; j < M2; j++) {
+      cd acc = 0.0;
+      for (int k = 0; k < M2; k++) acc += S[(size_t)i * M2 + k] * std::conj(S[(size_t)j * M2 + k]);
+      sQ[(size_t)i * M2 + j] = 0.5 * acc + (i == j ? 0.5 : 0.0);
+    }
+  std::vector<cd> lu = sQ, inv;
+  std::vector<int> piv;
+  cd phase;
+  double logdet;
+  if (!lu_factor(lu, M2, piv, phase, logdet)) return LHAF_EINVAL;
+  lu_inverse(lu, M2, piv, inv);
+  // A = X (I - sigma_Q^-1); for a pure state A = diag(B, B^*) and B = A[0:M, 0:M] = -(sigma_Q^-1)[M:2M, 0:M]
+  std::vector<lhaf_c128> B((size_t)M * M);
+  for (int i = 0; i < M; i++)
+    for (int j = 0; j < M; j++) {
+      const cd v = -inv[(size_t)(M + i) * M2 + j];
+      B[(size_t)i * M + j] = {v.real(), v.imag()};
+    }
+  // gamma = alpha_full^dag sigma_Q^-1 with alpha_full = (alpha, alpha^*); gamma_B = its first M entries;
+  // P0 = exp(-1/2 alpha_full^dag sigma_Q^-1 alpha_full) / sqrt(det sigma_Q)
+  std::vector<cd> af(M2, 0.0);
+  for (int i = 0; i < M; i++) {
+    const cd a = alpha ? cd(alpha[i].re, alpha[i].im) : cd(0.0);
+    af[i] = a;
+    af[M + i] = std::conj(a);
+  }
+  std::vector<lhaf_c128> gB(M);
+  cd quad = 0.0;
+  for (int j = 0; j < M2; j++) {
+    cd gj = 0.0;
+    for (int i = 0; i < M2; i++) gj += std::conj(af[i]) * inv[(size_t)i * M2 + j];
+    if (j < M) gB[j] = {gj.real(), gj.imag()};
+    quad += gj * af[j];
+  }
+  const double logP0 = -0.5 * quad.real() - 0.5 * logdet;
+  lhaf_c128 lh;
+  const lhaf_status st = lhaf(ctx, M, B.data(), gB.data(), n, flags & ~LHAF_DEVICE_PTRS, &lh, nullptr);
+  if (st != LHAF_OK) return st;
+  double log_fact = 0.0;
+  for (int i = 0; i < M; i++) log_fact += std::lgamma((double)n[i] + 1.0);
+  const double mag2 = lh.re * lh.re + lh.im * lh.im;
+  *prob = mag2 > 0.0 ? std::exp(logP0 - log_fact + std::log(mag2)) : 0.0;
+  if (lhaf_B) *lhaf_B = lh;
+  return LHAF_OK;
+}
