@@ -135,6 +135,19 @@ lhaf_status lhaf_batched(lhaf_ctx* ctx, int batch, int M, const lhaf_c128* B, co
                          const int32_t* reps, uint32_t flags, lhaf_c128* out, lhaf_status* item_status,
                          lhaf_stats* stats);
 
+/* Value and gradient of lhaf(B_n) (the paper has no gradient; it follows from the definition, App.
+ * B: the derivative of a matching sum with respect to one weight is the matching sum over the
+ * remaining indices, e.g. d lhaf / d gamma_m = n_m lhaf(n - e_m)). Computed by a per-term adjoint
+ * of the finite difference sieve on the GPU (FP64).
+ *   value : HOST, lhaf(B_n).
+ *   dB    : HOST M x M or NULL; dB[m][m'] = dB[m'][m] = d lhaf / d B_mm' with B symmetric (B_mm'
+ *           and B_m'm one variable; the library reads i <= j only).
+ *   dgamma: HOST M or NULL; d lhaf / d gamma_m. With gamma == NULL the loops are diag(B): their
+ *           derivative is added to dB[m][m] and dgamma is not written.
+ * Host pointers only (LHAF_DEVICE_PTRS and LHAF_FP32_TERMS give LHAF_EINVAL). */
+lhaf_status lhaf_grad(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128* gamma, const int32_t* reps,
+                      uint32_t flags, lhaf_c128* value, lhaf_c128* dB, lhaf_c128* dgamma);
+
 /* GBS pattern probability of a pure Gaussian state (App. A, Eq. mixed_prob with the pure-state
  * block form Eq. Adef): squeezed vacuum in every mode (a -> a cosh r - a^dag sinh r), then the
  * interferometer a -> U a, then the displacement alpha. On the host: the complex covariance

@@ -78,6 +78,8 @@ def _lib():
         L.lhaf_batched.restype = c.c_int
         L.gbs_pattern_prob.argtypes = [vp, c.c_int, vp, vp, vp, vp, c.c_uint32, ctypes.POINTER(c.c_double), vp]
         L.gbs_pattern_prob.restype = c.c_int
+        L.lhaf_grad.argtypes = [vp, c.c_int, vp, vp, vp, c.c_uint32, vp, vp, vp]
+        L.lhaf_grad.restype = c.c_int
         L.lhaf_fp64_probe.argtypes = [c.c_int, ctypes.POINTER(c.c_double)]
         L.lhaf_fp64_probe.restype = c.c_int
         _LIB = L
@@ -287,3 +289,16 @@ class Context:
                                           None if ah is None else ah.ctypes.data, nh.ctypes.data, flags,
                                           ctypes.byref(prob), lh.ctypes.data), "gbs_pattern_prob")
         return prob.value, complex(lh[0])
+
+    def lhaf_grad(self, B, gamma=None, reps=None, flags: int = 0):
+        """(lhaf(B_n), dB (M x M, symmetric-variable derivative), dgamma (M,) or None)."""
+        Bh = _host_c128(B)
+        M = Bh.shape[0]
+        gh = None if gamma is None else _host_c128(gamma)
+        r = _reps_arr(reps, M)
+        val = np.zeros(1, np.complex128)
+        dB = np.zeros((M, M), np.complex128)
+        dg = np.zeros(M, np.complex128)
+        _check(self._lib.lhaf_grad(self._h, M, Bh.ctypes.data, None if gh is None else gh.ctypes.data, _ptr(r), flags,
+                                   val.ctypes.data, dB.ctypes.data, dg.ctypes.data), "lhaf_grad")
+        return complex(val[0]), dB, (None if gh is None else dg)

@@ -52,10 +52,11 @@ extern "C" void lhaf_ctx_destroy(lhaf_ctx* ctx) {
   if (ctx->tev0) cudaEventDestroy(ctx->tev0);
   if (ctx->tev1) cudaEventDestroy(ctx->tev1);
   for (DevBuf* b : {&ctx->b_items, &ctx->b_units, &ctx->b_queue, &ctx->b_next, &ctx->b_partials, &ctx->b_unit_begin,
-                    &ctx->b_item_h, &ctx->b_chat, &ctx->b_chat32, &ctx->b_out, &ctx->b_stage, &ctx->b_wstage})
+                    &ctx->b_item_h, &ctx->b_chat, &ctx->b_chat32, &ctx->b_out, &ctx->b_stage, &ctx->b_wstage,
+                    &ctx->b_gpart, &ctx->b_gout})
     b->release();
   for (HostBuf* b : {&ctx->hb_items, &ctx->hb_units, &ctx->hb_queue, &ctx->hb_unit_begin, &ctx->hb_item_h,
-                     &ctx->hb_chat, &ctx->hb_chat32, &ctx->hb_out})
+                     &ctx->hb_chat, &ctx->hb_chat32, &ctx->hb_out, &ctx->hb_gout})
     b->release();
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   cudaSetDevice(prev);

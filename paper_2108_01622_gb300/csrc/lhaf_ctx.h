@@ -84,8 +84,8 @@ struct lhaf_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, tev0 = nullptr, tev1 = nullptr;
   // batched form
   DevBuf b_items, b_units, b_queue, b_next, b_partials, b_unit_begin, b_item_h, b_chat, b_chat32, b_out,
-      b_stage, b_wstage;
-  HostBuf hb_items, hb_units, hb_queue, hb_unit_begin, hb_item_h, hb_chat, hb_chat32, hb_out;
+      b_stage, b_wstage, b_gpart, b_gout;
+  HostBuf hb_items, hb_units, hb_queue, hb_unit_begin, hb_item_h, hb_chat, hb_chat32, hb_out, hb_gout;
   // measured best team size per problem shape
   std::map<TuneKey, int> tuned;
   std::mutex mu;

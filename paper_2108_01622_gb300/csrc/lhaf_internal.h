@@ -90,6 +90,14 @@ cudaError_t launch_batch_gather(const double2* B, long long B_stride, const doub
                                 long long gamma_stride, int M, const BatchItem* items, int n_items,
                                 double2* chat_pool, float2* chat32_pool, cudaStream_t stream);
 
+// Adjoint: shared bytes per team, occupancy, the value+gradient kernel and the cross-team sum.
+size_t grad_team_bytes(int nd, int H, int h, int bord);
+int grad_ctas_per_sm(int team, size_t smem_bytes);
+cudaError_t launch_grad(int team, const double2* chat, const TermParams& p, int grid, double* partials,
+                        double2* gpart, cudaStream_t stream);
+cudaError_t launch_grad_reduce(const double2* gpart, long long teams, int len, int h, double2* out,
+                               cudaStream_t stream);
+
 // Gather the bordered slot matrix from device B (M x M, upper triangle read) and gamma.
 // slot_mode: modes of the 2P slots (-1 = pad). gamma may be NULL (diag(B) is used).
 cudaError_t launch_gather(const double2* B, const double2* gamma, int M, const int* slot_mode_host,

@@ -178,17 +178,143 @@ __device__ __forceinline__ void build_cta_tables(const TermParams& p, unsigned c
 }
 
 // ---------------------------------------------------------------------------------------------
+// Adjoint of one term (reverse mode through Eq. ET_poly). With M = C X, u = v X (X = X_delta'),
+// g_k = Tr(M^k)/(2k) + u M^(k-1) v^T / 2 and f = [t^h] exp(sum g_k t^k), df/dg_k = e_{h-k}:
+//   df/dM = sum_k e_{h-k}/2 (M^(k-1))^T + sum_k e_{h-k}/2 sum_{i+l=k-2} (u M^i)^T (M^l v^T)^T
+//   df/du = sum_k e_{h-k}/2 (M^(k-1) v^T)^T,   df/dv|direct = sum_k e_{h-k}/2 u M^(k-1)
+//   dC = (df/dM) X,   dv = df/dv|direct + (df/du) X
+// The matrix polynomial sum_j c_j M^j (c_j = e_{h-1-j}/2) is evaluated by Horner's rule (dense
+// team matrix products); the second part is a Hankel-weighted sum of outer products of the Krylov
+// vectors x_l = M^l v^T and y_i = u M^i. Ga (n x n) and Gv (n) accumulate weight * (dC, dv).
+// ---------------------------------------------------------------------------------------------
+template <typename R, int G>
+__device__ __forceinline__ void term_adjoint(const typename Cx<R>::t* __restrict__ chat, int nd, int bord, int h,
+                                             const int* delta, const typename Cx<R>::t* e, double weight,
+                                             typename Cx<R>::t* Mb, typename Cx<R>::t* Xa, typename Cx<R>::t* Ta,
+                                             typename Cx<R>::t* Ga, typename Cx<R>::t* Gv, typename Cx<R>::t* xv,
+                                             typename Cx<R>::t* yu, int lt) {
+  using V = typename Cx<R>::t;
+  const int n = nd - bord;
+  const V zero = cmake<V>((R)0, (R)0);
+  const R wr = (R)weight;
+  // M = C X, x_0 = v^T, y_0 = u = v X
+  for (int w = lt; w < n * n; w += G) {
+    const int a = w / n, b = w - a * n;
+    const int dl = delta[b >> 1];
+    const V c = chat[(bord + a) * nd + bord + (b ^ 1)];
+    Mb[w] = cmake<V>(c.x * (R)dl, c.y * (R)dl);
+  }
+  for (int a = lt; a < n; a += G) xv[a] = bord ? chat[(bord + a) * nd] : zero;
+  team_sync<G>();
+  for (int b = lt; b < n; b += G) {
+    const V vb = xv[b ^ 1];
+    const R dl = (R)delta[b >> 1];
+    yu[b] = cmake<V>(vb.x * dl, vb.y * dl);
+  }
+  team_sync<G>();
+  // Krylov vectors x_l = M x_{l-1}, y_l = y_{l-1} M, l = 1..h-1
+  if (bord) {
+    for (int l = 1; l < h; l++) {
+      for (int w = lt; w < 2 * n; w += G) {
+        V acc = zero;
+        if (w < n) {
+          for (int j = 0; j < n; j++) cmac(acc, Mb[w * n + j], xv[(l - 1) * n + j]);
+          xv[l * n + w] = acc;
+        } else {
+          const int c = w - n;
+          for (int i = 0; i < n; i++) cmac(acc, yu[(l - 1) * n + i], Mb[i * n + c]);
+          yu[l * n + c] = acc;
+        }
+      }
+      team_sync<G>();
+    }
+  }
+  // Horner: X = sum_{j<h} c_j M^j, c_j = e_{h-1-j} / 2
+  V* X = Xa;
+  V* T = Ta;
+  {
+    const V c1 = cmake<V>((R)0.5 * e[0].x, (R)0.5 * e[0].y);  // c_{h-1}
+    const V c0 = (h >= 2) ? cmake<V>((R)0.5 * e[1].x, (R)0.5 * e[1].y) : zero;  // c_{h-2}
+    for (int w = lt; w < n * n; w += G) {
+      const int a = w / n, b = w - a * n;
+      V x = zero;
+      if (h >= 2) x = cmul(c1, Mb[w]);
+      if (a == b) {
+        const V d = (h >= 2) ? c0 : c1;
+        x.x += d.x;
+        x.y += d.y;
+      }
+      X[w] = x;
+    }
+    team_sync<G>();
+    for (int j = h - 3; j >= 0; j--) {
+      const V cj = cmake<V>((R)0.5 * e[h - 1 - j].x, (R)0.5 * e[h - 1 - j].y);
+      for (int w = lt; w < n * n; w += G) {
+        const int a = w / n, b = w - a * n;
+        V acc = (a == b) ? cj : zero;
+#pragma unroll 4
+        for (int l = 0; l < n; l++) cmac(acc, Mb[a * n + l], X[l * n + b]);
+        T[w] = acc;
+      }
+      team_sync<G>();
+      V* tmp = X;
+      X = T;
+      T = tmp;
+    }
+  }
+  // Z[i][c] = sum_{l <= h-2-i} e_{h-2-i-l}/2 x_l[c]  (i = 0..h-2), into the free Horner buffer
+  if (bord && h >= 2) {
+    for (int w = lt; w < (h - 1) * n; w += G) {
+      const int i = w / n, c = w - i * n;
+      V acc = zero;
+      for (int l = 0; l <= h - 2 - i; l++) cmac(acc, e[h - 2 - i - l], xv[l * n + c]);
+      T[w] = cmake<V>((R)0.5 * acc.x, (R)0.5 * acc.y);
+    }
+    team_sync<G>();
+  }
+  // accumulate weight * dC and weight * dv
+  for (int w = lt; w < n * n; w += G) {
+    const int a = w / n, b = w - a * n;
+    const int c = b ^ 1;
+    V gm = X[c * n + a];
+    if (bord)
+      for (int i = 0; i <= h - 2; i++) cmac(gm, yu[i * n + a], T[i * n + c]);
+    const R s = wr * (R)delta[b >> 1];
+    V g = Ga[w];
+    g.x = rfma(gm.x, s, g.x);
+    g.y = rfma(gm.y, s, g.y);
+    Ga[w] = g;
+  }
+  if (bord) {
+    for (int b = lt; b < n; b += G) {
+      V dv = zero, du = zero;
+      for (int k = 1; k <= h; k++) {
+        cmac(dv, e[h - k], yu[(k - 1) * n + b]);
+        cmac(du, e[h - k], xv[(k - 1) * n + (b ^ 1)]);
+      }
+      const R dl = (R)delta[b >> 1];
+      V g = Gv[b];
+      g.x = rfma((R)0.5 * wr, rfma(du.x, dl, dv.x), g.x);
+      g.y = rfma((R)0.5 * wr, rfma(du.y, dl, dv.y), g.y);
+      Gv[b] = g;
+    }
+  }
+  team_sync<G>();
+}
+
+// ---------------------------------------------------------------------------------------------
 // The sieve terms t = p.t_begin + team_global + r * p.total_teams (r < p.rounds, t < p.t_end)
 // of one loop hafnian, for the team of the calling thread. acc (lane 0 of the team) receives the
 // double-double sum (re_hi, re_lo, im_hi, im_lo) of weight * f. STAGE: instead of finishing a
 // term, write d_M and d_M - d_K to `stage` (coefficient-major, stage_ld terms per row, column
 // t - p.t_begin) and its weight to `wstage`.
 // ---------------------------------------------------------------------------------------------
-template <typename R, int G, bool STAGE>
+template <typename R, int G, bool STAGE, bool GRAD = false>
 __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict__ chat, const TermParams& p,
                                             unsigned char* smem, unsigned long long team_global,
                                             typename Cx<R>::t* __restrict__ stage, double* __restrict__ wstage,
-                                            long long stage_ld, double* acc) {
+                                            long long stage_ld, double* acc,
+                                            typename Cx<R>::t* __restrict__ gpart = nullptr) {
   using V = typename Cx<R>::t;
   constexpr int SG = G < 32 ? G : 32;  // lanes of the first warp of a team
 
@@ -211,6 +337,20 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
   const V zero = cmake<V>((R)0, (R)0);
   const V one = cmake<V>((R)1, (R)0);
   double acc_re = 0.0, acc_re_lo = 0.0, acc_im = 0.0, acc_im_lo = 0.0;
+
+  // adjoint buffers (GRAD): X, T (max(n^2, h n) each), Ga (n^2), Gv (n), x_l and y_l (h n each)
+  const int ng = nd - bord;
+  const int nbuf = (ng * ng > h * ng) ? ng * ng : h * ng;
+  V* gX = reinterpret_cast<V*>(reinterpret_cast<unsigned char*>(ts) + ((sizeof(TeamScratch) + 15) & ~(size_t)15));
+  V* gT = gX + nbuf;
+  V* gA = gT + nbuf;
+  V* gV = gA + ng * ng;
+  V* gx = gV + ng;
+  V* gy = gx + h * ng;
+  if constexpr (GRAD) {
+    for (int w = lt; w < ng * ng + ng; w += G) gA[w] = zero;  // gV follows gA
+    team_sync<G>();
+  }
 
   for (unsigned long long rnd = 0; rnd < p.rounds; rnd++) {
     unsigned long long t = p.t_begin + team_global + rnd * p.total_teams;
@@ -604,7 +744,14 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
         }
       }
       team_sync<G>();
+      if constexpr (GRAD) {
+        term_adjoint<R, G>(chat, nd, bord, h, ts->delta, Se, ts->weight, W, gX, gT, gA, gV, gx, gy, lt);
+      }
     }
+  }
+  if constexpr (GRAD) {
+    V* o = gpart + (size_t)team_global * (size_t)(ng * ng + ng);
+    for (int w = lt; w < ng * ng + ng; w += G) o[w] = gA[w];
   }
 
   acc[0] = acc_re;
@@ -848,6 +995,48 @@ __global__ void batch_gather_kernel(const double2* __restrict__ B, long long B_s
     if (chat_pool) chat_pool[it.chat_off + w] = c;
     if (chat32_pool) chat32_pool[it.chat_off + w] = make_float2((float)c.x, (float)c.y);
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Value and adjoint of one loop hafnian: like terms_kernel (inline series), plus per-team gradient
+// partials (n x n for the slot matrix, then n for the loop vector) in gpart.
+// ---------------------------------------------------------------------------------------------
+template <int G>
+__global__ void __launch_bounds__(cta_of(G))
+grad_kernel(const double2* __restrict__ chat, const __grid_constant__ TermParams p, double* __restrict__ partials,
+            double2* __restrict__ gpart) {
+  constexpr int CTA = cta_of(G);
+  constexpr int TEAMS = CTA / G;
+  extern __shared__ __align__(16) unsigned char smem[];
+  build_cta_tables<double, CTA>(p, smem);
+  __syncthreads();
+  const int team = threadIdx.x / G;
+  const int lt = threadIdx.x - team * G;
+  const unsigned long long team_global = (unsigned long long)blockIdx.x * TEAMS + team;
+  double acc[4];
+  sieve_terms<double, G, false, true>(chat, p, smem, team_global, nullptr, nullptr, 0, acc, gpart);
+  if (lt == 0) {
+    double* o = partials + 4ull * team_global;
+    o[0] = acc[0];
+    o[1] = acc[1];
+    o[2] = acc[2];
+    o[3] = acc[3];
+  }
+}
+
+// out[k] = 2^-h * sum over teams of gpart[team][k] (double-double), k < len.
+__global__ void grad_reduce_kernel(const double2* __restrict__ gpart, long long teams, int len, int h,
+                                   double2* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= len) return;
+  double rh = 0.0, rl = 0.0, ih = 0.0, il = 0.0;
+  for (long long t = 0; t < teams; t++) {
+    const double2 v = gpart[t * len + k];
+    dd_add(rh, rl, v.x);
+    dd_add(ih, il, v.y);
+  }
+  const double s1 = __longlong_as_double((long long)(1023 - h) << 52);
+  out[k] = make_double2((rh + rl) * s1, (ih + il) * s1);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1123,6 +1312,54 @@ cudaError_t launch_series(bool fp32, const void* stage, const double* wstage, lo
 }
 
 size_t cta_table_bytes(bool fp32, int Hl, int H) { return items_bytes_of(fp32, Hl, H); }
+
+size_t grad_team_bytes(int nd, int H, int h, int bord) {
+  const int n = nd - bord;
+  const size_t nbuf = (size_t)((n * n > h * n) ? n * n : h * n);
+  size_t b = team_shared_bytes(false, nd, H, 0, false) + ((sizeof(TeamScratch) + 15) & ~(size_t)15);
+  b += (2 * nbuf + (size_t)n * n + n + 2 * (size_t)h * n) * sizeof(double2);
+  return (b + 15) & ~(size_t)15;
+}
+
+template <int G> static const void* gptr() { return (const void*)grad_kernel<G>; }
+
+static const void* pick_grad(int team) {
+  switch (team) {
+    case 8: return gptr<8>();
+    case 16: return gptr<16>();
+    case 32: return gptr<32>();
+    case 64: return gptr<64>();
+    case 128: return gptr<128>();
+  }
+  return nullptr;
+}
+
+int grad_ctas_per_sm(int team, size_t smem_bytes) {
+  const void* k = pick_grad(team);
+  if (!k) return 0;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, cta_of(team), smem_bytes) != cudaSuccess) return 0;
+  return n;
+}
+
+cudaError_t launch_grad(int team, const double2* chat, const TermParams& p, int grid, double* partials, double2* gpart,
+                        cudaStream_t stream) {
+  const void* k = pick_grad(team);
+  if (!k) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)p.items_bytes + (size_t)teams_per_cta(team) * p.team_bytes;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&chat, (void*)&p, (void*)&partials, (void*)&gpart};
+  return cudaLaunchKernel(k, dim3(grid), dim3(cta_of(team)), args, smem, stream);
+}
+
+cudaError_t launch_grad_reduce(const double2* gpart, long long teams, int len, int h, double2* out,
+                               cudaStream_t stream) {
+  if (len <= 0) return cudaSuccess;
+  grad_reduce_kernel<<<(len + 127) / 128, 128, 0, stream>>>(gpart, teams, len, h, out);
+  return cudaGetLastError();
+}
 
 template <typename R, int G> static const void* bptr() { return (const void*)batched_kernel<R, G>; }
 

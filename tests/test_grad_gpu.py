@@ -1,0 +1,124 @@
+"""Gradients from the adjoint kernel (lhaf_grad, through the C ABI) against the minor identity of
+the definition (oracle and GPU minors), central finite differences (h = 1e-6), and the chain rule
+through the GBS log-probability (torch.autograd)."""
+import numpy as np
+import pytest
+
+from oracle import lhaf_oracle as lo
+from paper_2108_01622_gb300 import workloads as wl
+from tests.libutil import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lg = ensure_built()
+    c = lg.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("reps", [(1, 1, 1, 1), (2, 1, 0, 3), (3, 2, 2, 1), (1, 2, 1), (4, 1, 1, 0, 2), (2, 2, 2)])
+@pytest.mark.parametrize("loops", [True, False])
+def test_grad_matches_minor_identity(ctx, reps, loops):
+    p = wl.small_problem(seed=sum(reps) * 3 + len(reps), M=len(reps), reps=reps, loops=loops)
+    val, dB, dg = ctx.lhaf_grad(p.B, p.gamma, p.reps)
+    ref = lo.lhaf_repeated(p.B, p.gamma, p.reps)
+    dB_ref, dg_ref = lo.lhaf_grad_minor(p.B, p.gamma, p.reps)
+    scale = max(np.abs(dB_ref).max(), np.abs(dg_ref).max(), 1e-300)
+    assert abs(val - ref) <= 1e-10 * abs(ref) + 1e-14
+    assert np.abs(dB - dB_ref).max() <= 1e-9 * scale
+    assert np.abs(dg - dg_ref).max() <= 1e-9 * scale
+
+
+def test_grad_gamma_none_folds_loops_into_diagonal(ctx):
+    p = wl.small_problem(seed=4, M=3, reps=(2, 1, 2))
+    d = np.diag(p.B).copy()
+    val, dB, dg = ctx.lhaf_grad(p.B, None, p.reps)
+    dB_ref, dg_ref = lo.lhaf_grad_minor(p.B, d, p.reps)
+    dB_ref[np.diag_indices(3)] += dg_ref
+    assert dg is None
+    assert np.abs(dB - dB_ref).max() <= 1e-9 * np.abs(dB_ref).max()
+
+
+def test_grad_central_differences(ctx):
+    p = wl.single_lhaf_24(seed=6, n_photons=14)
+    val, dB, dg = ctx.lhaf_grad(p.B, p.gamma, p.reps)
+    h = 1e-6
+    rng = np.random.default_rng(0)
+    occ = np.nonzero(p.reps)[0]
+    for _ in range(4):
+        i, j = sorted(rng.choice(occ, size=2, replace=False))
+        E = np.zeros_like(p.B)
+        E[i, j] = E[j, i] = 1.0
+        fd = (ctx.lhaf(p.B + h * E, p.gamma, p.reps) - ctx.lhaf(p.B - h * E, p.gamma, p.reps)) / (2 * h)
+        assert abs(fd - dB[i, j]) <= 1e-6 * max(abs(dB[i, j]), abs(val))
+        m = rng.choice(occ)
+        e = np.zeros_like(p.gamma)
+        e[m] = 1.0
+        fd = (ctx.lhaf(p.B, p.gamma + h * e, p.reps) - ctx.lhaf(p.B, p.gamma - h * e, p.reps)) / (2 * h)
+        assert abs(fd - dg[m]) <= 1e-6 * max(abs(dg[m]), abs(val))
+
+
+def test_grad_32_photon_outcome_against_gpu_minors(ctx):
+    # 32 photons over a 40-mode state (collisions allowed): d lhaf / d B_mm' = n_m n_m' lhaf(n - e_m - e_m')
+    b = wl.gradient_batch(seed=4, count=2)
+    B, g, reps = b.B, b.gammas[0], b.reps[0]
+    val, dB, dg = ctx.lhaf_grad(B, g, reps)
+    assert abs(val - ctx.lhaf(B, g, reps)) <= 1e-10 * abs(val)
+    occ = np.nonzero(reps)[0]
+    for m, mp in [(occ[0], occ[1]), (occ[2], occ[5]), (occ[3], occ[3])]:
+        r = reps.copy()
+        if m == mp:
+            if r[m] < 2:
+                continue
+            r[m] -= 2
+            ref = reps[m] * (reps[m] - 1) / 2 * ctx.lhaf(B, g, r)
+        else:
+            r[m] -= 1
+            r[mp] -= 1
+            ref = reps[m] * reps[mp] * ctx.lhaf(B, g, r)
+        assert abs(dB[m, mp] - ref) <= 1e-8 * abs(ref), (m, mp)
+    for m in occ[:4]:
+        r = reps.copy()
+        r[m] -= 1
+        ref = reps[m] * ctx.lhaf(B, g, r)
+        assert abs(dg[m] - ref) <= 1e-8 * abs(ref)
+
+
+def test_log_prob_chain_rule_squeezing_displacement_phases(ctx):
+    import torch
+
+    from paper_2108_01622_gb300.autograd import gbs_log_prob_torch
+
+    rng = np.random.default_rng(12)
+    M = 5
+    U0 = wl.haar_unitary(rng, M)
+    n = np.array([2, 1, 0, 1, 2], np.int32)
+    r = torch.tensor(rng.uniform(0.3, 0.8, M), dtype=torch.float64, requires_grad=True)
+    a = torch.tensor(wl.complex_normal(rng, M, 0.2), dtype=torch.complex128, requires_grad=True)
+    phi = torch.tensor(rng.uniform(0, 1, M), dtype=torch.float64, requires_grad=True)
+
+    def logp(r_, a_, phi_):
+        U = torch.from_numpy(U0) @ torch.diag(torch.exp(1j * phi_.to(torch.complex128)))
+        return gbs_log_prob_torch(U, r_, a_, n, ctx)
+
+    L = logp(r, a, phi)
+    L.backward()
+    h = 1e-6
+    with torch.no_grad():
+        for k in range(M):
+            e = torch.zeros(M, dtype=torch.float64)
+            e[k] = h
+            fd = (logp(r + e, a, phi) - logp(r - e, a, phi)) / (2 * h)
+            assert abs(fd.item() - r.grad[k].item()) <= 1e-5 * max(1.0, abs(fd.item()))
+            fd = (logp(r, a, phi + e) - logp(r, a, phi - e)) / (2 * h)
+            assert abs(fd.item() - phi.grad[k].item()) <= 1e-5 * max(1.0, abs(fd.item()))
+            # real loss of a complex input: torch's gradient is dL/dRe + i dL/dIm
+            fr = (logp(r, a + e.to(torch.complex128), phi) - logp(r, a - e.to(torch.complex128), phi)) / (2 * h)
+            fi = (logp(r, a + 1j * e.to(torch.complex128), phi) - logp(r, a - 1j * e.to(torch.complex128), phi)) / (2 * h)
+            assert abs(complex(fr.item(), fi.item()) - complex(a.grad[k].item())) <= 1e-5 * max(1.0, abs(fr.item()))
