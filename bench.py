@@ -204,7 +204,7 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=dev)
     p = wl.collision_lhaf_40(seed=2)
     T, nd, h, P = lg.plan(p.reps, has_loops=False)
-    ctx = lg.Context(local_rank, stream=torch.cuda.current_stream(dev).cuda_stream)
+    ctx = lg.Context(local_rank)  # ordered on torch's current stream
     Bd = torch.from_numpy(p.B).to(dev)
     gd = torch.from_numpy(p.gamma).to(dev)
     flags = lg.NO_LOOPS
@@ -253,6 +253,8 @@ def run_ours(args, rank, world, local_rank):
         e2e_times.append(time.perf_counter() - t0)
     e2e_ms = statistics.median(e2e_times) * 1e3
 
+    extras = {} if args.no_extras else run_extras(ctx, torch, dev, lg, wl)
+
     avg_kernel_ms = statistics.mean(kern_ms)
     flops = stats["flops_model"]
     achieved = flops / (avg_kernel_ms * 1e-3) / 1e12
@@ -277,6 +279,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "result": [val.real, val.imag],
     }
+    line.update(extras)
     if cpu_base is not None:
         line["cpu_baseline"] = {k: cpu_base[k] for k in ("value", "unit", "cores", "kind", "sample")}
         line["cpu_baseline"]["ms_per_lhaf"] = cpu_base["ms_per_lhaf"]
@@ -288,6 +291,98 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+def _timed(torch, fn, reps=3):
+    """Median device time (ms) of fn() over reps calls (CUDA events on the current stream)."""
+    times = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    return statistics.median(times)
+
+
+def run_extras(ctx, torch, dev, lg, wl):
+    """The rest of the metric, each on its own workload (untimed by the step loop above):
+    ms per 60-photon loop hafnian (projected from a timed slice of its sieve terms), the FP32-term
+    variant on the same slice, batched vs one call per item on a chain-rule batch, and the adjoint."""
+    out = {}
+    # 60-photon collision-free lhaf (100-mode Haar, r ~ U[1.2, 1.8]): 2^29 terms of dimension 61
+    p60 = wl.large_lhaf_60(seed=5)
+    T60, nd60, h60, _ = lg.plan(p60.reps)
+    B60 = torch.from_numpy(p60.B).to(dev)
+    g60 = torch.from_numpy(p60.gamma).to(dev)
+    S = 1 << 17
+    ctx.lhaf_range(B60, g60, p60.reps, 0, 4096)  # tunes the team size for this shape
+    ms64 = _timed(torch, lambda: ctx.lhaf_range(B60, g60, p60.reps, 0, S), reps=2)
+    ctx.lhaf_range(B60, g60, p60.reps, 0, 4096, flags=lg.FP32_TERMS)
+    ms32 = _timed(torch, lambda: ctx.lhaf_range(B60, g60, p60.reps, 0, S, flags=lg.FP32_TERMS), reps=2)
+    fl = lg.flops_per_term(nd60, h60, True)
+    out["lhaf60"] = {"workload": "60-photon collision-free loop hafnian, 100-mode Haar, r~U[1.2,1.8], complex gamma",
+                     "terms_per_lhaf": T60, "n_dim": nd60, "h": h60, "timed_terms": S,
+                     "ms_per_60_photon_lhaf_projected": ms64 * T60 / S, "fp64_tflops": fl * S / (ms64 * 1e-3) / 1e12,
+                     "fp32_terms_ms_per_lhaf_projected": ms32 * T60 / S, "fp32_speedup": ms64 / ms32,
+                     "note": "projected = timed slice x (terms / slice); every term costs the same"}
+    # batched vs one call per item: 512 loop hafnians of the chain-rule batch (N in 10..40)
+    b = wl.chain_rule_batch(seed=3, count=512)
+    R = np.array(b.reps)
+    Gd = torch.from_numpy(np.array(b.gammas)).to(dev)
+    Bd = torch.from_numpy(b.B).to(dev)
+    ob = torch.empty(len(R), dtype=torch.complex128, device=dev)
+    op = torch.empty(len(R), dtype=torch.complex128, device=dev)
+    ctx.lhaf_batched(Bd, Gd, R, out=ob)
+    for i in range(len(R)):  # warm the per-shape tuning cache of the single-call path
+        ctx.lhaf(Bd, Gd[i], R[i], out=op[i:i + 1])
+    torch.cuda.synchronize()
+    tb = _timed(torch, lambda: ctx.lhaf_batched(Bd, Gd, R, out=ob), reps=2)
+
+    def plain():
+        for i in range(len(R)):
+            ctx.lhaf(Bd, Gd[i], R[i], out=op[i:i + 1])
+
+    tp = _timed(torch, plain, reps=2)
+    d = (ob - op).abs() / op.abs()
+    out["batched"] = {"workload": "chain-rule batch: 512 loop hafnians, 50-mode lossy GBS state, N~U{10..40}",
+                      "batched_ms": tb, "plain_ms": tp, "batched_over_plain_speedup": tp / tb,
+                      "max_rel_diff": float(d.max().item())}
+    # small items only: many short loop hafnians, where one launch per item is launch-bound
+    bs = wl.chain_rule_batch(seed=7, count=2048, n_lo=8, n_hi=16)
+    Rs = np.array(bs.reps)
+    Gs = torch.from_numpy(np.array(bs.gammas)).to(dev)
+    Bs = torch.from_numpy(bs.B).to(dev)
+    obs = torch.empty(len(Rs), dtype=torch.complex128, device=dev)
+    ops_ = torch.empty(len(Rs), dtype=torch.complex128, device=dev)
+    ctx.lhaf_batched(Bs, Gs, Rs, out=obs)
+    for i in range(len(Rs)):
+        ctx.lhaf(Bs, Gs[i], Rs[i], out=ops_[i:i + 1])
+    tbs = _timed(torch, lambda: ctx.lhaf_batched(Bs, Gs, Rs, out=obs), reps=2)
+
+    def plain_s():
+        for i in range(len(Rs)):
+            ctx.lhaf(Bs, Gs[i], Rs[i], out=ops_[i:i + 1])
+
+    tps = _timed(torch, plain_s, reps=2)
+    out["batched_small"] = {"workload": "2048 loop hafnians, N~U{8..16}, same state family",
+                            "batched_ms": tbs, "plain_ms": tps, "batched_over_plain_speedup": tps / tbs}
+    # adjoint: one 32-photon outcome of a 40-mode state
+    gb = wl.gradient_batch(seed=4, count=2)
+    import time as _t
+    ctx.lhaf_grad(gb.B, gb.gammas[0], gb.reps[0])
+    t0 = _t.perf_counter()
+    ctx.lhaf_grad(gb.B, gb.gammas[0], gb.reps[0])
+    tg = (_t.perf_counter() - t0) * 1e3
+    t0 = _t.perf_counter()
+    ctx.lhaf(gb.B, gb.gammas[0], gb.reps[0])
+    tv = (_t.perf_counter() - t0) * 1e3
+    Tg, ndg, hg, _ = lg.plan(gb.reps[0])
+    out["grad"] = {"workload": "value + d/dB + d/dgamma of one 32-photon outcome, 40-mode state",
+                   "terms": Tg, "n_dim": ndg, "h": hg, "grad_ms": tg, "value_ms": tv, "grad_over_value": tg / tv}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -295,6 +390,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
     args = ap.parse_args()
     rank, world, local_rank = rank_info()
     if args.impl == "reference":

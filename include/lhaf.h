@@ -84,8 +84,8 @@ typedef struct {
                            recurrence and the series, 8 flops each (lhaf_flops_per_term) */
 } lhaf_stats;
 
-/* Create a context on `device`. cuda_stream: a cudaStream_t to order work on, or NULL for a
- * stream the context creates and owns. Allocates the context's device workspace.
+/* Create a context on `device`. cuda_stream: a cudaStream_t to order work on (cudaStreamLegacy or
+ * cudaStreamPerThread included), or NULL for a non-blocking stream the context creates and owns. Allocates the context's device workspace.
  * Returns LHAF_ECUDA if the device cannot be used, LHAF_ENOMEM on allocation failure. */
 lhaf_status lhaf_ctx_create(lhaf_ctx** ctx, int device, void* cuda_stream);
 
@@ -94,6 +94,10 @@ void lhaf_ctx_destroy(lhaf_ctx* ctx);
 
 /* Static description of a status code. */
 const char* lhaf_strerror(lhaf_status status);
+
+/* The failing CUDA call and CUDA's message of the last LHAF_ECUDA returned on this thread ("" if
+ * none). Valid until the next call on this thread. */
+const char* lhaf_last_error(void);
 
 /* Plan only (host, no GPU): the greedy pairing of App. B.3 for `reps`, returning the number of
  * sieve terms after halving, the working dimension and the degree. `has_loops` != 0 counts the

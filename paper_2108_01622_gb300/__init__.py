@@ -34,7 +34,9 @@ STATUS = {0: "LHAF_OK", 1: "LHAF_EINVAL", 2: "LHAF_ETOOBIG", 3: "LHAF_ECUDA", 4:
 class LhafError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
-        super().__init__(f"{where}: {STATUS.get(status, status)} ({_lib().lhaf_strerror(status).decode()})")
+        detail = _lib().lhaf_last_error().decode() if status == 3 else ""
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({_lib().lhaf_strerror(status).decode()})"
+                         + (f" [{detail}]" if detail else ""))
 
 
 class Stats(ctypes.Structure):
@@ -62,6 +64,8 @@ def _lib():
         L.lhaf_ctx_destroy.restype = None
         L.lhaf_strerror.argtypes = [c.c_int]
         L.lhaf_strerror.restype = c.c_char_p
+        L.lhaf_last_error.argtypes = []
+        L.lhaf_last_error.restype = c.c_char_p
         L.lhaf_plan.argtypes = [c.c_int, vp, c.c_uint32, c.c_int, ctypes.POINTER(c.c_uint64),
                                 ctypes.POINTER(c.c_int32), ctypes.POINTER(c.c_int32), ctypes.POINTER(c.c_int32)]
         L.lhaf_plan.restype = c.c_int
@@ -165,6 +169,11 @@ class Context:
                     stream = torch.cuda.current_stream(device).cuda_stream
             except ImportError:
                 pass
+        if stream == 0:
+            # torch's default stream is the legacy default stream (handle 0), which the library would
+            # read as "create a private stream": pass cudaStreamLegacy instead so that work is ordered
+            # with torch's own kernels and events
+            stream = 1
         self.stream = stream
         h = ctypes.c_void_p()
         _check(self._lib.lhaf_ctx_create(ctypes.byref(h), device, stream), "lhaf_ctx_create")

@@ -7,6 +7,7 @@
 #include <complex>
 #include <cstdint>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -18,6 +19,18 @@
 #include "lhaf_ctx.h"
 
 using namespace lhafgpu;
+
+namespace lhafgpu {
+static thread_local char g_last_error[512] = "";
+int record_cuda(cudaError_t e, const char* what) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
+  cudaGetLastError();  // clear a non-sticky error so it is not reported twice
+  return (lhaf_status)record_cuda(cudaPeekAtLastError(), "lhaf_api.cpp:28");
+}
+void record_message(const char* msg) { std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+}  // namespace lhafgpu
+
+extern "C" const char* lhaf_last_error(void) { return lhafgpu::g_last_error; }
 
 extern "C" const char* lhaf_strerror(lhaf_status s) {
   switch (s) {
@@ -73,7 +86,7 @@ extern "C" lhaf_status lhaf_ctx_create(lhaf_ctx** out, int device, void* cuda_st
   c->device = device;
   if (cudaSetDevice(device) != cudaSuccess) {
     delete c;
-    return LHAF_ECUDA;
+    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "lhaf_api.cpp:89");
   }
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
   if (cuda_stream) {
@@ -81,7 +94,7 @@ extern "C" lhaf_status lhaf_ctx_create(lhaf_ctx** out, int device, void* cuda_st
   } else {
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
       delete c;
-      return LHAF_ECUDA;
+      return (lhaf_status)record_cuda(cudaPeekAtLastError(), "lhaf_api.cpp:97");
     }
     c->own_stream = true;
   }
@@ -224,9 +237,14 @@ int pick_team(lhaf_ctx* ctx, bool fp32, const Plan& pl, bool staged, int family,
       p.rounds = (S + p.total_teams - 1) / p.total_teams;
       p.t_begin = 0;
       p.t_end = S;
+      // the trial stages its own S terms at stride S (rows x S entries, within the buffer the
+      // caller sized for rows x chunk with S <= chunk)
       void* stage = staged ? ctx->d_stage : nullptr;
-      const long long stage_ld = staged ? (long long)ctx->wstage_terms : 0;
-      if (staged && (uint64_t)stage_ld < S) continue;
+      const long long stage_ld = staged ? (long long)S : 0;
+      if (staged) {
+        const size_t rows = pl.bord ? 2 * (size_t)pl.h + 1 : (size_t)pl.h;
+        if (rows * S * (fp32 ? sizeof(float2) : sizeof(double2)) > ctx->stage_bytes || S > ctx->wstage_terms) continue;
+      }
       float ms = 0.f;
       for (int rep = 0; rep < 2; rep++) {
         cudaEventRecord(ctx->tev0, ctx->stream);
@@ -379,19 +397,19 @@ lhaf_status run_terms(lhaf_ctx* ctx, const Plan& pl, uint32_t flags, uint64_t tb
     } else if (staged) {
       e = launch_terms(fp32, team, chat, p, (int)grid, ctx->d_partials, ctx->stream, ctx->d_stage, ctx->d_wstage,
                        (long long)chunk);
-      if (e != cudaSuccess) return LHAF_ECUDA;
+      if (const cudaError_t e_ = (e); e_ != cudaSuccess) return (lhaf_status)record_cuda(e_, "e");
       e = launch_series(fp32, ctx->d_stage, ctx->d_wstage, (long long)n, (long long)chunk, pl.h, pl.bord, p.plain,
                         ctx->d_partials, ctx->stream);
-      if (e != cudaSuccess) return LHAF_ECUDA;
+      if (const cudaError_t e_ = (e); e_ != cudaSuccess) return (lhaf_status)record_cuda(e_, "e");
       nparts = series_blocks((long long)n);
     } else {
       e = launch_terms(fp32, team, chat, p, (int)grid, ctx->d_partials, ctx->stream);
-      if (e != cudaSuccess) return LHAF_ECUDA;
+      if (const cudaError_t e_ = (e); e_ != cudaSuccess) return (lhaf_status)record_cuda(e_, "e");
       nparts = (long long)p.total_teams;
     }
     const bool last = c1 >= te;
     e = launch_reduce(ctx->d_partials, nparts, pl.h, acc_dd, last ? val_dst : nullptr, ctx->stream, ci > 0 ? 1 : 0);
-    if (e != cudaSuccess) return LHAF_ECUDA;
+    if (const cudaError_t e_ = (e); e_ != cudaSuccess) return (lhaf_status)record_cuda(e_, "e");
     c0 = c1;
     ci++;
   } while (c0 < te);
@@ -423,7 +441,7 @@ lhaf_status lhaf_common(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c12
       if (reps[i] < 0) return LHAF_EINVAL;
   }
   std::lock_guard<std::mutex> lock(ctx->mu);
-  if (cudaSetDevice(ctx->device) != cudaSuccess) return LHAF_ECUDA;
+  if (const cudaError_t e_ = (cudaSetDevice(ctx->device)); e_ != cudaSuccess) return (lhaf_status)record_cuda(e_, "cudaSetDevice");
   Plan pl;
   // Loop border: with host inputs, detected from gamma; with device inputs, present unless the
   // caller declares LHAF_NO_LOOPS.
@@ -468,10 +486,10 @@ lhaf_status lhaf_common(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c12
   if (st != LHAF_OK) return st;
   if (!dev) {
     cudaError_t e = cudaMemcpyAsync(ctx->h_out, ctx->d_out, 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
-    if (e != cudaSuccess) return LHAF_ECUDA;
+    if (const cudaError_t e_ = (e); e_ != cudaSuccess) return (lhaf_status)record_cuda(e_, "e");
   }
   if (!dev || timed) {
-    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return LHAF_ECUDA;
+    if (const cudaError_t e_ = (cudaStreamSynchronize(ctx->stream)); e_ != cudaSuccess) return (lhaf_status)record_cuda(e_, "cudaStreamSynchronize");
   }
   if (timed) {
     float ms = 0.f;
@@ -486,7 +504,7 @@ lhaf_status lhaf_common(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c12
       out->im = ctx->h_out[5];
     }
   }
-  return cudaGetLastError() == cudaSuccess ? LHAF_OK : LHAF_ECUDA;
+  return LHAF_OK;
 }
 
 }  // namespace

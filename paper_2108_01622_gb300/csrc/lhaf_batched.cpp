@@ -36,7 +36,7 @@ extern "C" lhaf_status lhaf_batched(lhaf_ctx* ctx, int batch, int M, const lhaf_
   const bool fp32 = (flags & LHAF_FP32_TERMS) != 0;
   const long long B_stride = per_item_B ? (long long)M * M : 0;
   std::lock_guard<std::mutex> lock(ctx->mu);
-  if (cudaSetDevice(ctx->device) != cudaSuccess) return LHAF_ECUDA;
+  if (const cudaError_t e_ = (cudaSetDevice(ctx->device)); e_ != cudaSuccess) return (lhaf_status)record_cuda(e_, "cudaSetDevice");
 
   // ---- plans ----
   std::vector<Plan> plans(batch);
@@ -128,11 +128,11 @@ extern "C" lhaf_status lhaf_batched(lhaf_ctx* ctx, int batch, int M, const lhaf_
   (void)cs;
   // descriptors first (the device gather reads them)
   if (cudaMemcpyAsync(ctx->b_items.p, hitems, sizeof(BatchItem) * batch, cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return LHAF_ECUDA;
+    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "lhaf_batched.cpp:131");
   if (dev) {
     if (launch_batch_gather((const double2*)B, B_stride, (const double2*)gamma, M, M, (const BatchItem*)ctx->b_items.p,
                             batch, (double2*)ctx->b_chat.p, fp32 ? (float2*)ctx->b_chat32.p : nullptr, s) != cudaSuccess)
-      return LHAF_ECUDA;
+      return (lhaf_status)record_cuda(cudaPeekAtLastError(), "lhaf_batched.cpp:135");
   } else {
     if (!ctx->hb_chat.reserve(sizeof(double2) * std::max<long long>(pool, 1))) return LHAF_ENOMEM;
     std::complex<double>* hc = static_cast<std::complex<double>*>(ctx->hb_chat.p);
@@ -144,10 +144,10 @@ extern "C" lhaf_status lhaf_batched(lhaf_ctx* ctx, int batch, int M, const lhaf_
       float2* h32 = static_cast<float2*>(ctx->hb_chat32.p);
       for (long long e = 0; e < pool; e++) h32[e] = make_float2((float)hc[e].real(), (float)hc[e].imag());
       if (cudaMemcpyAsync(ctx->b_chat32.p, h32, sizeof(float2) * pool, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return LHAF_ECUDA;
+        return (lhaf_status)record_cuda(cudaPeekAtLastError(), "lhaf_batched.cpp:147");
     } else if (pool > 0) {
       if (cudaMemcpyAsync(ctx->b_chat.p, hc, sizeof(double2) * pool, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return LHAF_ECUDA;
+        return (lhaf_status)record_cuda(cudaPeekAtLastError(), "lhaf_batched.cpp:150");
     }
   }
 
@@ -284,26 +284,26 @@ extern "C" lhaf_status lhaf_batched(lhaf_ctx* ctx, int batch, int M, const lhaf_
             cudaMemcpyAsync(ctx->b_item_h.p, ctx->hb_item_h.p, sizeof(int) * batch, cudaMemcpyHostToDevice, s) ==
                 cudaSuccess &&
             cudaMemsetAsync(ctx->b_next.p, 0, sizeof(int), s) == cudaSuccess;
-  if (!ok) return LHAF_ECUDA;
+  if (!ok) return (lhaf_status)record_cuda(cudaPeekAtLastError(), "lhaf_batched.cpp:287");
   if (stats) cudaEventRecord(ctx->ev0, s);
   if (n_units > 0) {
     if (launch_batched(fp32, team, chat_pool, (const BatchItem*)ctx->b_items.p, (const BatchUnit*)ctx->b_units.p,
                        (const int*)ctx->b_queue.p, n_units, (int*)ctx->b_next.p, (double*)ctx->b_partials.p,
                        (int)team_bytes, (int)items_bytes, (int)grid_b, s, region_elems ? ctx->b_stage.p : nullptr,
                        region_elems ? (double*)ctx->b_wstage.p : nullptr) != cudaSuccess)
-      return LHAF_ECUDA;
+      return (lhaf_status)record_cuda(cudaPeekAtLastError(), "lhaf_batched.cpp:294");
   }
   double2* dout = dev ? (double2*)out : (double2*)ctx->b_out.p;
   if (launch_batch_reduce((const double*)ctx->b_partials.p, (const int*)ctx->b_unit_begin.p, (const int*)ctx->b_item_h.p,
                           TEAMS, batch, dout, s) != cudaSuccess)
-    return LHAF_ECUDA;
+    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "lhaf_batched.cpp:299");
   if (stats) cudaEventRecord(ctx->ev1, s);
   if (!dev) {
     if (cudaMemcpyAsync(ctx->hb_out.p, ctx->b_out.p, sizeof(double2) * batch, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-      return LHAF_ECUDA;
+      return (lhaf_status)record_cuda(cudaPeekAtLastError(), "lhaf_batched.cpp:303");
   }
   if (!dev || stats) {
-    if (cudaStreamSynchronize(s) != cudaSuccess) return LHAF_ECUDA;
+    if (const cudaError_t e_ = (cudaStreamSynchronize(s)); e_ != cudaSuccess) return (lhaf_status)record_cuda(e_, "cudaStreamSynchronize");
   }
   if (stats) {
     float ms = 0.f;
@@ -311,5 +311,5 @@ extern "C" lhaf_status lhaf_batched(lhaf_ctx* ctx, int batch, int M, const lhaf_
     stats->kernel_ms = ms;
   }
   if (!dev) std::memcpy(out, ctx->hb_out.p, sizeof(double2) * batch);
-  return cudaGetLastError() == cudaSuccess ? LHAF_OK : LHAF_ECUDA;
+  return LHAF_OK;
 }

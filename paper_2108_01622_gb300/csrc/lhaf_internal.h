@@ -103,4 +103,8 @@ cudaError_t launch_grad_reduce(const double2* gpart, long long teams, int len, i
 cudaError_t launch_gather(const double2* B, const double2* gamma, int M, const int* slot_mode_host,
                           int P, int bord, double2* chat, float2* chat32, cudaStream_t stream);
 
+// Failed CUDA call: remember "what: CUDA message" for lhaf_last_error() and return LHAF_ECUDA (3).
+int record_cuda(cudaError_t e, const char* what);
+void record_message(const char* msg);
+
 }  // namespace lhafgpu

@@ -168,7 +168,7 @@ __device__ __forceinline__ void build_cta_tables(const TermParams& p, unsigned c
   const int Hl = p.Hl;
   for (int w = threadIdx.x; w < p.n_items; w += CTA) {
     int e = 0, base = 0;
-    while (base + (Hl - 1 - e) <= w) {
+    while (e < Hl - 2 && base + (Hl - 1 - e) <= w) {
       base += Hl - 1 - e;
       e++;
     }
@@ -886,6 +886,10 @@ batched_kernel(const typename Cx<R>::t* __restrict__ chat_pool, const BatchItem*
       sp.items_bytes = items_bytes;
     }
     __syncthreads();
+    // a descriptor outside the compiled limits is skipped (its partials stay as they are)
+    if (sp.nd < 2 || sp.nd > kMaxDim || sp.P > kMaxPairs || sp.h > kMaxDegree || sp.Hl > sp.nd ||
+        sp.n_items != sp.Hl * (sp.Hl - 1) / 2)
+      continue;
     build_cta_tables<R, CTA>(sp, smem);
     __syncthreads();
     double acc[4];
@@ -1274,9 +1278,15 @@ static const void* pick_kernel(bool fp32, int team, bool staged) {
 int max_ctas_per_sm(bool fp32, int team, size_t smem_bytes, bool staged) {
   const void* k = pick_kernel(fp32, team, staged);
   if (!k) return 0;
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess) return 0;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, cta_of(team), smem_bytes) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, cta_of(team), smem_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   return n;
 }
 
@@ -1337,9 +1347,15 @@ static const void* pick_grad(int team) {
 int grad_ctas_per_sm(int team, size_t smem_bytes) {
   const void* k = pick_grad(team);
   if (!k) return 0;
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess) return 0;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, cta_of(team), smem_bytes) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, cta_of(team), smem_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   return n;
 }
 
@@ -1377,9 +1393,15 @@ static const void* pick_batched(bool fp32, int team) {
 int batched_ctas_per_sm(bool fp32, int team, size_t smem_bytes) {
   const void* k = pick_batched(fp32, team);
   if (!k) return 0;
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess) return 0;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, cta_of(team), smem_bytes) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, cta_of(team), smem_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   return n;
 }
 

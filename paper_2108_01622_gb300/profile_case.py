@@ -27,7 +27,7 @@ def main():
     else:
         raise SystemExit(f"unknown workload {name}")
     dev = torch.device("cuda", 0)
-    with lg.Context(0, stream=torch.cuda.current_stream(dev).cuda_stream) as ctx:
+    with lg.Context(0) as ctx:
         Bd = torch.from_numpy(p.B).to(dev)
         gd = torch.from_numpy(p.gamma).to(dev)
         for _ in range(calls):

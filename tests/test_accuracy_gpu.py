@@ -1,0 +1,71 @@
+"""Accuracy at larger sizes (App. B.4 accuracy discussion): the 30-photon sub-instance of the
+60-photon workload against the oracle (FP64 path, and the FP32-term variant's stated error), and
+the paper's block-diagonal construction lhaf(diag(A1, A2)) = lhaf(A1) lhaf(A2) with every sieve
+pair crossing the blocks."""
+import numpy as np
+import pytest
+
+from oracle import lhaf_oracle as lo
+from paper_2108_01622_gb300 import workloads as wl
+from tests.libutil import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+# Stated error of the FP32-term variant (per-term arithmetic in FP32, double-double accumulation)
+# on GBS-shaped 30-photon inputs.
+FP32_STATED_REL_ERROR = 1e-2
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lg = ensure_built()
+    c = lg.Context(0)
+    yield c
+    c.close()
+
+
+def sub30():
+    p = wl.large_lhaf_60(seed=5)
+    occ = np.nonzero(p.reps)[0]
+    r30 = np.zeros_like(p.reps)
+    r30[occ[:30]] = 1
+    return p, r30
+
+
+def test_30_photon_sub_instance_fp64_and_fp32(ctx):
+    p, r30 = sub30()
+    ref = lo.lhaf_repeated(p.B, p.gamma, r30)
+    got = ctx.lhaf(p.B, p.gamma, r30)
+    assert abs(got - ref) <= 1e-10 * abs(ref)
+    got32 = ctx.lhaf(p.B, p.gamma, r30, flags=0x2)
+    err32 = abs(got32 - ref) / abs(ref)
+    print(f"FP32-term variant, 30 photons: relative error {err32:.3e}")
+    assert err32 <= FP32_STATED_REL_ERROR
+    plain = ctx.lhaf(p.B, p.gamma, r30, flags=0x4)
+    assert abs(plain - ref) <= 1e-10 * abs(ref)
+
+
+def test_block_diagonal_identity_40_photons(ctx):
+    rng = np.random.default_rng(44)
+    n = 20
+    U1, U2 = wl.haar_unitary(rng, n), wl.haar_unitary(rng, n)
+    A1 = wl.kernel_from_squeezing(U1, rng.uniform(1.0, 1.5, n))
+    A2 = wl.kernel_from_squeezing(U2, rng.uniform(1.0, 1.5, n))
+    g1, g2 = wl.complex_normal(rng, n), wl.complex_normal(rng, n)
+    # interleave the blocks (block 1 on even modes, block 2 on odd modes): the greedy pairs
+    # (0,1), (2,3), ... then each couple one index of each block
+    Bb = np.zeros((2 * n, 2 * n), complex)
+    Bb[0::2, 0::2] = A1
+    Bb[1::2, 1::2] = A2
+    gb = np.zeros(2 * n, complex)
+    gb[0::2] = g1
+    gb[1::2] = g2
+    ones = np.ones(n, np.int32)
+    ref = lo.lhaf_repeated(A1, g1, ones) * lo.lhaf_repeated(A2, g2, ones)
+    got = ctx.lhaf(Bb, gb, np.ones(2 * n, np.int32))
+    err = abs(got - ref) / abs(ref)
+    print(f"block-diagonal identity, 40 photons: relative error {err:.3e}")
+    assert err <= 1e-10

@@ -155,3 +155,17 @@ def test_plain_accumulation_close(ctx):
     a = ctx.lhaf(p.B, p.gamma, p.reps)
     b = ctx.lhaf(p.B, p.gamma, p.reps, flags=0x4)
     assert rel(b, a) < 1e-11
+
+
+def test_staging_reuse_with_more_coefficient_rows(ctx):
+    # A staged call with many terms and few coefficient rows, then a new problem shape with more
+    # rows and few terms (autotuned on its first call): both must match the oracle.
+    p1 = wl.collision_lhaf_40(seed=2)  # no loops: h = 20 rows, 34,560 terms
+    assert rel(ctx.lhaf(p1.B, p1.gamma, p1.reps), lo.lhaf_repeated(p1.B, p1.gamma, p1.reps)) < TOL
+    b = wl.chain_rule_batch(seed=3, count=64)
+    for i in range(len(b.reps)):
+        r = b.reps[i]
+        if 30 <= r.sum() <= 34:  # loops: 2h + 1 rows
+            got = ctx.lhaf(b.B, b.gammas[i], r)
+            assert rel(got, lo.lhaf_repeated(b.B, b.gammas[i], r)) < TOL
+            break
