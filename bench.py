@@ -30,6 +30,7 @@ METRIC = "lhaf sieve terms/s (collision-pattern loop hafnian, FP64)"
 UNIT = "terms/s"
 WORKLOAD = ("collision-pattern loop hafnian: 100-mode Haar interferometer, r ~ U[1.0,1.6], gamma = 0, "
             "40 photons over 22 modes with counts 1..4 (seeded multinomial), complex128, repeated-pair sieve")
+KERNEL_NAME = "batched_kernel (FP64 sieve terms of the zero-digit groups, persistent)"
 NOMINAL_FP64_GFLOPS = 152 * 4 * 0.5 * 2 * 2.070  # SMs x sub-partitions x FMA lanes/clk x 2 flops x GHz
 
 
@@ -204,6 +205,7 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=dev)
     p = wl.collision_lhaf_40(seed=2)
     T, nd, h, P = lg.plan(p.reps, has_loops=False)
+    groups = lg.plan_groups(p.reps, has_loops=False)
     ctx = lg.Context(local_rank)  # ordered on torch's current stream
     Bd = torch.from_numpy(p.B).to(dev)
     gd = torch.from_numpy(p.gamma).to(dev)
@@ -226,12 +228,14 @@ def run_ours(args, rank, world, local_rank):
                            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv")
     time.sleep(0.3)
     stats = None
+    launches = 0
     for s in range(args.steps):
         flush.zero_()
         starts[s].record()
         _, stats = ctx.lhaf(Bd, gd, p.reps, flags=flags, out=out, stats=True)
         ends[s].record()
         kern_ms.append(stats["kernel_ms"])
+        launches += stats["launches"]
     torch.cuda.synchronize()
     clocks = sampler.stop()
     if world > 1:
@@ -246,6 +250,7 @@ def run_ours(args, rank, world, local_rank):
     val = complex(out.cpu()[0])
 
     # e2e: the public host-pointer call (pinned staging copies inside the library) per step
+    _, est = ctx.lhaf(p.B, p.gamma, p.reps, stats=True)  # bytes the host path copies per call
     e2e_times = []
     for s in range(max(3, args.steps // 4)):
         t0 = time.perf_counter()
@@ -263,11 +268,12 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "terms_per_lhaf": T, "n_dim": nd, "h": h, "pairs": P,
-                   "team": stats["team"], "l2": "flushed between steps (256 MiB write, outside step events)",
+                   "team": stats["team"], "zero_digit_groups": groups,
+                   "l2": "flushed between steps (256 MiB write, outside step events)",
                    "parallelism": f"{world} independent loop hafnians, one per GPU"},
         "ms_per_lhaf": total_ms / args.steps,
-        "gpu_launches": 3 * args.steps,
-        "roofline": {"bound": "alu", "kernel": "terms_kernel (FP64 sieve terms)",
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": KERNEL_NAME if groups else "terms_kernel (FP64 sieve terms)",
                      "achieved": achieved, "peak": NOMINAL_FP64_GFLOPS / 1e3, "unit": "TFLOP/s",
                      "frac": achieved / (NOMINAL_FP64_GFLOPS / 1e3), "traffic": None,
                      "peak_source": "derived: 152 SMs x 4 sub-partitions x 0.5 FP64 FMA lanes/clk x 2 x 2.070 GHz",
@@ -275,7 +281,7 @@ def run_ours(args, rank, world, local_rank):
                      "frac_of_probe": achieved / (fp64_gflops / 1e3),
                      "flops_per_launch": flops, "avg_launch_ms": avg_kernel_ms},
         "e2e": {"value": T / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_lhaf": e2e_ms,
-                "h2d_bytes_per_step": nd * nd * 16, "d2h_bytes_per_step": 48},
+                "h2d_bytes_per_step": est["h2d_bytes"], "d2h_bytes_per_step": est["d2h_bytes"]},
         "clocks": clocks,
         "result": [val.real, val.imag],
     }
@@ -345,9 +351,15 @@ def run_extras(ctx, torch, dev, lg, wl):
 
     tp = _timed(torch, plain, reps=2)
     d = (ob - op).abs() / op.abs()
+    og = torch.empty(len(R), dtype=torch.complex128, device=dev)
+    with ctx.batched_plan(Bd, Gd, R) as plan:
+        plan.run(Bd, Gd, out=og)
+        tg_ = _timed(torch, lambda: plan.run(Bd, Gd, out=og), reps=2)
+    dg = (og - op).abs() / op.abs()
     out["batched"] = {"workload": "chain-rule batch: 512 loop hafnians, 50-mode lossy GBS state, N~U{10..40}",
-                      "batched_ms": tb, "plain_ms": tp, "batched_over_plain_speedup": tp / tb,
-                      "max_rel_diff": float(d.max().item())}
+                      "batched_ms": tb, "graph_replay_ms": tg_, "plain_ms": tp,
+                      "batched_over_plain_speedup": tp / tb, "graph_over_plain_speedup": tp / tg_,
+                      "max_rel_diff": float(max(d.max().item(), dg.max().item()))}
     # small items only: many short loop hafnians, where one launch per item is launch-bound
     bs = wl.chain_rule_batch(seed=7, count=2048, n_lo=8, n_hi=16)
     Rs = np.array(bs.reps)
@@ -365,8 +377,13 @@ def run_extras(ctx, torch, dev, lg, wl):
             ctx.lhaf(Bs, Gs[i], Rs[i], out=ops_[i:i + 1])
 
     tps = _timed(torch, plain_s, reps=2)
+    ogs = torch.empty(len(Rs), dtype=torch.complex128, device=dev)
+    with ctx.batched_plan(Bs, Gs, Rs) as plan:
+        plan.run(Bs, Gs, out=ogs)
+        tgs = _timed(torch, lambda: plan.run(Bs, Gs, out=ogs), reps=3)
     out["batched_small"] = {"workload": "2048 loop hafnians, N~U{8..16}, same state family",
-                            "batched_ms": tbs, "plain_ms": tps, "batched_over_plain_speedup": tps / tbs}
+                            "batched_ms": tbs, "graph_replay_ms": tgs, "plain_ms": tps,
+                            "batched_over_plain_speedup": tps / tbs, "graph_over_plain_speedup": tps / tgs}
     # adjoint: one 32-photon outcome of a 40-mode state
     gb = wl.gradient_batch(seed=4, count=2)
     import time as _t

@@ -64,6 +64,9 @@ typedef enum {
 #define LHAF_NO_LOOPS 0x10u          /* declare gamma == 0 on the occupied modes (skips the loop
                                         border); with host pointers this is detected by itself */
 #define LHAF_BATCH_B_PER_ITEM 0x20u  /* lhaf_batched: B holds one M x M matrix per item */
+#define LHAF_NO_ZERO_SPLIT 0x40u     /* evaluate the middle digits of even-eta pairs (delta' = 0) on
+                                        the full working matrix instead of in zero-digit groups with
+                                        those slots deleted (same sum; for comparisons) */
 
 /* Compiled limits. */
 #define LHAF_MAX_DIM 64      /* working dimension n_dim = 2 * pairs (+1 loop border) */
@@ -82,6 +85,10 @@ typedef struct {
   double flops_model;   /* algorithmic real flops of this call: per term, the complex
                            multiply-adds of the elimination Hessenberg reduction, La Budde's
                            recurrence and the series, 8 flops each (lhaf_flops_per_term) */
+  uint64_t h2d_bytes;   /* bytes this call copied host -> device (inputs, descriptors) */
+  uint64_t d2h_bytes;   /* bytes this call copied device -> host (results) */
+  int32_t launches;     /* CUDA kernels this call launched (tuning trials excluded) */
+  int32_t reserved;
 } lhaf_stats;
 
 /* Create a context on `device`. cuda_stream: a cudaStream_t to order work on (cudaStreamLegacy or
@@ -100,8 +107,14 @@ const char* lhaf_strerror(lhaf_status status);
 const char* lhaf_last_error(void);
 
 /* Plan only (host, no GPU): the greedy pairing of App. B.3 for `reps`, returning the number of
- * sieve terms after halving, the working dimension and the degree. `has_loops` != 0 counts the
- * loop border. Any output pointer may be NULL. */
+ * evaluated sieve terms after halving, the largest working dimension and the degree. `has_loops`
+ * != 0 counts the loop border. Any output pointer may be NULL.
+ * Evaluated terms: a pair with even eta has a middle digit (delta' = 0) whose two slot columns
+ * vanish, so unless LHAF_NO_ZERO_SPLIT is given the sieve runs as zero-digit groups: for every
+ * subset Z of the even pairs, Z at their middle digit with their slots deleted and the others
+ * without it, each group halved by the sign symmetry on one of its own pairs. Terms are numbered
+ * group after group (subsets in increasing bit order over the even pairs in pair order), which is
+ * the numbering lhaf_range uses. */
 lhaf_status lhaf_plan(int M, const int32_t* reps, uint32_t flags, int has_loops, uint64_t* terms,
                       int32_t* n_dim, int32_t* h, int32_t* pairs);
 
@@ -109,6 +122,10 @@ lhaf_status lhaf_plan(int M, const int32_t* reps, uint32_t flags, int has_loops,
  * out: one lhaf_c128 (host, or device with LHAF_DEVICE_PTRS). stats: host pointer or NULL. */
 lhaf_status lhaf(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128* gamma,
                  const int32_t* reps, uint32_t flags, lhaf_c128* out, lhaf_stats* stats);
+
+/* Number of zero-digit groups the sieve of `reps` runs as (0: no split, one sieve on the full
+ * working matrix), with the same arguments as lhaf_plan (host only). */
+lhaf_status lhaf_plan_groups(int M, const int32_t* reps, uint32_t flags, int has_loops, int32_t* groups);
 
 /* Partial sieve sum over the evaluated-term index range [term_begin, term_end) (terms numbered
  * 0 .. terms-1 as reported by lhaf_plan). partial_dd receives 4 doubles (re_hi, re_lo, im_hi,
@@ -138,6 +155,30 @@ double lhaf_flops_per_term(int n_dim, int h, int bordered);
 lhaf_status lhaf_batched(lhaf_ctx* ctx, int batch, int M, const lhaf_c128* B, const lhaf_c128* gamma,
                          const int32_t* reps, uint32_t flags, lhaf_c128* out, lhaf_status* item_status,
                          lhaf_stats* stats);
+
+/* Batched plan: lhaf_batched planned once for fixed patterns and replayed for new values of B and
+ * gamma. Creation does the host planning of every item (greedy pairs, App. B.3), tunes the team
+ * size on (B, gamma), sizes all buffers and captures the launches (slot-matrix gather, persistent
+ * kernel, per-item reduction) in a CUDA graph; each exec copies the new B and gamma into the
+ * plan's buffers, replays the graph on the context's stream and returns the values. The structure
+ * may not depend on values: the loop border is present unless LHAF_NO_LOOPS, so items whose loop
+ * weights are all zero cost what they would with loops (the result is the same).
+ *   create: B, gamma, reps and flags as for lhaf_batched (B and gamma host, or device with
+ *           LHAF_DEVICE_PTRS; they are only read during the call). gamma NULL fixes loops = diag(B)
+ *           for every exec. The plan keeps a copy of reps. Errors: LHAF_EINVAL for bad arguments;
+ *           per-item planning failures are reported by each exec's item_status, not here.
+ *   exec  : B (same layout and size as at creation), gamma (NULL exactly when it was NULL at
+ *           creation), out (batch lhaf_c128), item_status (HOST, batch entries, or NULL) and stats
+ *           as for lhaf_batched; host or device pointers per the creation flags. Host-pointer execs
+ *           are synchronous; device-pointer execs are stream-ordered. Execs of one plan must not
+ *           overlap (they share its buffers); a plan is tied to its context.
+ *   destroy: frees the plan (NULL is ignored); no exec of it may still be running. */
+typedef struct lhaf_batch_plan lhaf_batch_plan;
+lhaf_status lhaf_batched_plan_create(lhaf_ctx* ctx, int batch, int M, const lhaf_c128* B, const lhaf_c128* gamma,
+                                     const int32_t* reps, uint32_t flags, lhaf_batch_plan** plan);
+lhaf_status lhaf_batched_plan_exec(lhaf_batch_plan* plan, const lhaf_c128* B, const lhaf_c128* gamma,
+                                   lhaf_c128* out, lhaf_status* item_status, lhaf_stats* stats);
+void lhaf_batched_plan_destroy(lhaf_batch_plan* plan);
 
 /* Value and gradient of lhaf(B_n) (the paper has no gradient; it follows from the definition, App.
  * B: the derivative of a matching sum with respect to one weight is the matching sum over the

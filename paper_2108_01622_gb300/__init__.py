@@ -26,6 +26,7 @@ PLAIN_ACCUM = 0x4
 NO_REPEAT_SPEEDUP = 0x8
 NO_LOOPS = 0x10
 BATCH_B_PER_ITEM = 0x20
+NO_ZERO_SPLIT = 0x40
 
 STATUS = {0: "LHAF_OK", 1: "LHAF_EINVAL", 2: "LHAF_ETOOBIG", 3: "LHAF_ECUDA", 4: "LHAF_ETIMEOUT",
           5: "LHAF_ENOMEM", 6: "LHAF_ECANCELLED"}
@@ -42,7 +43,8 @@ class LhafError(RuntimeError):
 class Stats(ctypes.Structure):
     _fields_ = [("terms", ctypes.c_uint64), ("n_dim", ctypes.c_int32), ("h", ctypes.c_int32),
                 ("pairs", ctypes.c_int32), ("team", ctypes.c_int32), ("kernel_ms", ctypes.c_double),
-                ("flops_model", ctypes.c_double)]
+                ("flops_model", ctypes.c_double), ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
+                ("launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -69,6 +71,8 @@ def _lib():
         L.lhaf_plan.argtypes = [c.c_int, vp, c.c_uint32, c.c_int, ctypes.POINTER(c.c_uint64),
                                 ctypes.POINTER(c.c_int32), ctypes.POINTER(c.c_int32), ctypes.POINTER(c.c_int32)]
         L.lhaf_plan.restype = c.c_int
+        L.lhaf_plan_groups.argtypes = [c.c_int, vp, c.c_uint32, c.c_int, ctypes.POINTER(c.c_int32)]
+        L.lhaf_plan_groups.restype = c.c_int
         L.lhaf.argtypes = [vp, c.c_int, vp, vp, vp, c.c_uint32, vp, ctypes.POINTER(Stats)]
         L.lhaf.restype = c.c_int
         L.lhaf_range.argtypes = [vp, c.c_int, vp, vp, vp, c.c_uint32, c.c_uint64, c.c_uint64, vp,
@@ -84,6 +88,12 @@ def _lib():
         L.gbs_pattern_prob.restype = c.c_int
         L.lhaf_grad.argtypes = [vp, c.c_int, vp, vp, vp, c.c_uint32, vp, vp, vp]
         L.lhaf_grad.restype = c.c_int
+        L.lhaf_batched_plan_create.argtypes = [vp, c.c_int, c.c_int, vp, vp, vp, c.c_uint32, ctypes.POINTER(vp)]
+        L.lhaf_batched_plan_create.restype = c.c_int
+        L.lhaf_batched_plan_exec.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
+        L.lhaf_batched_plan_exec.restype = c.c_int
+        L.lhaf_batched_plan_destroy.argtypes = [vp]
+        L.lhaf_batched_plan_destroy.restype = None
         L.lhaf_fp64_probe.argtypes = [c.c_int, ctypes.POINTER(c.c_double)]
         L.lhaf_fp64_probe.restype = c.c_int
         _LIB = L
@@ -135,6 +145,14 @@ def plan(reps: Sequence[int], flags: int = 0, has_loops: bool = True) -> Tuple[i
     _check(_lib().lhaf_plan(len(r), r.ctypes.data, flags, int(has_loops), ctypes.byref(T), ctypes.byref(nd),
                             ctypes.byref(h), ctypes.byref(P)), "lhaf_plan")
     return T.value, nd.value, h.value, P.value
+
+
+def plan_groups(reps: Sequence[int], flags: int = 0, has_loops: bool = True) -> int:
+    """Number of zero-digit groups the sieve runs as (0: a single sieve on the full matrix)."""
+    r = np.ascontiguousarray(np.asarray(reps, dtype=np.int32))
+    g = ctypes.c_int32()
+    _check(_lib().lhaf_plan_groups(len(r), r.ctypes.data, flags, int(has_loops), ctypes.byref(g)), "lhaf_plan_groups")
+    return g.value
 
 
 def flops_per_term(n_dim: int, h: int, bordered: bool) -> float:
@@ -285,6 +303,11 @@ class Context:
             return res, status, st.as_dict()
         return res, status
 
+    def batched_plan(self, B, gammas, reps, flags: int = 0) -> "BatchedPlan":
+        """A BatchedPlan for the patterns `reps` (batch x M): planned, tuned on (B, gammas) and
+        captured in a CUDA graph once; BatchedPlan.run evaluates new values of B and gammas."""
+        return BatchedPlan(self, B, gammas, reps, flags)
+
     def gbs_pattern_prob(self, U, r, alpha, n, flags: int = 0):
         """(P(n), lhaf(B_n)) for the pure state (U, r, alpha) (App. A, Eq. mixed_prob)."""
         Uh = _host_c128(U)
@@ -311,3 +334,79 @@ class Context:
         _check(self._lib.lhaf_grad(self._h, M, Bh.ctypes.data, None if gh is None else gh.ctypes.data, _ptr(r), flags,
                                    val.ctypes.data, dB.ctypes.data, dg.ctypes.data), "lhaf_grad")
         return complex(val[0]), dB, (None if gh is None else dg)
+
+
+class BatchedPlan:
+    """lhaf_batched for fixed patterns, replayed from a captured CUDA graph (include/lhaf.h,
+    lhaf_batched_plan_*). Inputs are numpy arrays (host) or torch CUDA tensors (device), as chosen
+    at creation; B and gammas keep their creation shapes."""
+
+    def __init__(self, ctx: Context, B, gammas, reps, flags: int = 0):
+        self._ctx = ctx
+        self._lib = ctx._lib
+        r = np.ascontiguousarray(np.asarray(reps, dtype=np.int32))
+        if r.ndim != 2:
+            raise ValueError("reps must be batch x M")
+        self.batch, self.M = r.shape
+        self.dev = _is_torch(B) and B.is_cuda
+        self.with_gamma = gammas is not None
+        if self.dev:
+            flags |= DEVICE_PTRS
+        self.flags = flags
+        Bp, gp, keep = self._marshal(B, gammas)
+        h = ctypes.c_void_p()
+        _check(self._lib.lhaf_batched_plan_create(ctx._h, self.batch, self.M, Bp, gp, r.ctypes.data, flags,
+                                                  ctypes.byref(h)), "lhaf_batched_plan_create")
+        del keep
+        self._h = h
+
+    def _marshal(self, B, gammas):
+        if (gammas is not None) != self.with_gamma:
+            raise ValueError("gammas must be given exactly when they were given at creation")
+        if self.dev:
+            import torch
+
+            Bt = B.to(torch.complex128).contiguous()
+            gt = None if gammas is None else gammas.to(torch.complex128).contiguous()
+            return Bt.data_ptr(), (None if gt is None else gt.data_ptr()), (Bt, gt)
+        Bh = _host_c128(B)
+        gh = None if gammas is None else _host_c128(gammas)
+        return Bh.ctypes.data, (None if gh is None else gh.ctypes.data), (Bh, gh)
+
+    def run(self, B, gammas=None, stats: bool = False, out=None):
+        """Values of the batch for new B and gammas: (values, item_status[, stats])."""
+        if not getattr(self, "_h", None):
+            raise RuntimeError("plan is closed")
+        Bp, gp, keep = self._marshal(B, gammas)
+        st = Stats()
+        status = np.zeros(self.batch, dtype=np.int32)
+        if self.dev:
+            import torch
+
+            if out is None:
+                out = torch.empty(self.batch, dtype=torch.complex128, device=B.device)
+            res, optr = out, out.data_ptr()
+        else:
+            res = np.zeros(self.batch, np.complex128)
+            optr = res.ctypes.data
+        _check(self._lib.lhaf_batched_plan_exec(self._h, Bp, gp, optr, status.ctypes.data,
+                                                ctypes.byref(st) if stats else None), "lhaf_batched_plan_exec")
+        del keep
+        return (res, status, st.as_dict()) if stats else (res, status)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lhaf_batched_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -64,13 +64,10 @@ extern "C" void lhaf_ctx_destroy(lhaf_ctx* ctx) {
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   if (ctx->tev0) cudaEventDestroy(ctx->tev0);
   if (ctx->tev1) cudaEventDestroy(ctx->tev1);
-  for (DevBuf* b : {&ctx->b_items, &ctx->b_units, &ctx->b_queue, &ctx->b_next, &ctx->b_partials, &ctx->b_unit_begin,
-                    &ctx->b_item_h, &ctx->b_chat, &ctx->b_chat32, &ctx->b_out, &ctx->b_stage, &ctx->b_wstage,
-                    &ctx->b_gpart, &ctx->b_gout})
-    b->release();
-  for (HostBuf* b : {&ctx->hb_items, &ctx->hb_units, &ctx->hb_queue, &ctx->hb_unit_begin, &ctx->hb_item_h,
-                     &ctx->hb_chat, &ctx->hb_chat32, &ctx->hb_out, &ctx->hb_gout})
-    b->release();
+  ctx->bw.release();
+  ctx->b_gpart.release();
+  ctx->b_gout.release();
+  ctx->hb_gout.release();
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   cudaSetDevice(prev);
   delete ctx;
@@ -118,15 +115,34 @@ extern "C" lhaf_status lhaf_ctx_create(lhaf_ctx** out, int device, void* cuda_st
   return LHAF_OK;
 }
 
+// Terms the sieve evaluates: the plan's, or the sum over its zero-digit groups.
+static uint64_t evaluated_terms(const Plan& pl, uint32_t flags) {
+  std::vector<Plan> subs;
+  if (pl.N == 0 || (flags & LHAF_NO_ZERO_SPLIT) || !split_zero_digits(pl, subs)) return pl.T;
+  uint64_t T = 0;
+  for (const Plan& s : subs) T += s.T;
+  return T;
+}
+
 extern "C" lhaf_status lhaf_plan(int M, const int32_t* reps, uint32_t flags, int has_loops, uint64_t* terms,
                                  int32_t* n_dim, int32_t* h, int32_t* pairs) {
   Plan pl;
   lhaf_status st = build_plan(M, reps, flags, has_loops != 0, pl);
   if (st != LHAF_OK) return st;
-  if (terms) *terms = pl.T;
+  if (terms) *terms = evaluated_terms(pl, flags);
   if (n_dim) *n_dim = pl.nd;
   if (h) *h = pl.h;
   if (pairs) *pairs = pl.P;
+  return LHAF_OK;
+}
+
+extern "C" lhaf_status lhaf_plan_groups(int M, const int32_t* reps, uint32_t flags, int has_loops, int32_t* groups) {
+  if (!groups) return LHAF_EINVAL;
+  Plan pl;
+  lhaf_status st = build_plan(M, reps, flags, has_loops != 0, pl);
+  if (st != LHAF_OK) return st;
+  std::vector<Plan> subs;
+  *groups = (pl.N > 0 && !(flags & LHAF_NO_ZERO_SPLIT) && split_zero_digits(pl, subs)) ? (int32_t)subs.size() : 0;
   return LHAF_OK;
 }
 
@@ -162,6 +178,10 @@ void fill_params(const Plan& pl, bool fp32, bool staged, int team, uint32_t flag
   p.hp = pl.hp;
   p.hp_even = pl.hp_even;
   p.plain = (flags & LHAF_PLAIN_ACCUM) ? 1 : 0;
+  p.skip_mask = 0u;
+  for (int q = 0; q < pl.P && q < (int)pl.skip.size(); q++)
+    if (pl.skip[q]) p.skip_mask |= 1u << q;
+  p.wscale = pl.wscale;
   p.n_items = pl.Hl * (pl.Hl - 1) / 2;
   p.team_bytes = (int)team_shared_bytes(fp32, pl.nd, pl.H, pl.P, staged);
   p.items_bytes = (int)(cta_shared_bytes(fp32, team, pl.nd, pl.H, pl.Hl, pl.P, staged) -
@@ -172,10 +192,38 @@ void fill_params(const Plan& pl, bool fp32, bool staged, int team, uint32_t flag
   }
 }
 
-// Team size (lanes per term). LHAF_TEAM forces one. Otherwise each candidate that fits in shared
-// memory runs a short slice of real terms (two rounds of the resident grid), timed with CUDA
-// events; the fastest per term is cached for the problem shape. Problems too small to time
-// meaningfully use a model of FP64 lane utilisation times sub-partition coverage instead.
+// Resident CTAs per SM used for a launch: the occupancy limit, or fewer if LHAF_CTAS_PER_SM asks.
+int ctas_per_sm_override(int occ) {
+  const char* env = std::getenv("LHAF_CTAS_PER_SM");
+  const int c = env ? std::atoi(env) : 0;
+  return (c > 0 && c < occ) ? c : occ;
+}
+
+// Grid for n terms at tpc teams per CTA and at most max_ctas resident CTAs: the fewest rounds,
+// then the fewest CTAs that finish n terms in that many rounds (so that at most tpc - 1 teams of
+// the last round evaluate a padding term instead of a whole round's worth).
+uint64_t balanced_grid(uint64_t n, int tpc, uint64_t max_ctas, unsigned long long* rounds) {
+  if (max_ctas < 1) max_ctas = 1;
+  uint64_t grid = (n + tpc - 1) / tpc;
+  if (grid > max_ctas) grid = max_ctas;
+  if (grid < 1) grid = 1;
+  uint64_t r = (n + grid * tpc - 1) / (grid * tpc);
+  if (r < 1) r = 1;
+  const uint64_t teams = (n + r - 1) / r;
+  grid = (teams + tpc - 1) / tpc;
+  if (grid < 1) grid = 1;
+  *rounds = (n + grid * tpc - 1) / (grid * tpc);
+  if (*rounds < 1) *rounds = 1;
+  return grid;
+}
+
+// Team size (lanes per term) and resident CTAs per SM. LHAF_TEAM forces the team size. Otherwise
+// each candidate that fits in shared memory runs a short slice of real terms (two rounds of the
+// resident grid), timed with CUDA events, at its occupancy limit and at the largest smaller CTA
+// count that gives every SM sub-partition the same number of warps (the sub-partitions share the
+// SM's FP64 unit, and one with an extra warp finishes last); the fastest per term is cached for
+// the problem shape. Problems too small to time meaningfully use a model of FP64 lane utilisation
+// times sub-partition coverage instead.
 int pick_team(lhaf_ctx* ctx, bool fp32, const Plan& pl, bool staged, int family, const void* chat,
               int* ctas_per_sm) {
   const char* env = std::getenv("LHAF_TEAM");
@@ -212,62 +260,73 @@ int pick_team(lhaf_ctx* ctx, bool fp32, const Plan& pl, bool staged, int family,
   const TuneKey key{fp32 ? 1 : 0, staged ? 1 : 0, pl.nd, pl.Hl, pl.h, pl.bord, family};
   auto it = ctx->tuned.find(key);
   if (it != ctx->tuned.end()) {
-    *ctas_per_sm = occ_of(it->second);
-    return it->second;
+    *ctas_per_sm = it->second >> 16;
+    return it->second & 0xffff;
   }
   const char* env_tune = std::getenv("LHAF_AUTOTUNE");
   const bool tune = !(env_tune && env_tune[0] == '0');
-  int best_g = model_g;
+  int best_g = model_g, best_occ = occ_of(model_g);
   if (tune && chat) {
     double best_per_term = 1e300;
-    for (int c = 0; c < 5; c++) {
+    bool too_small = false;
+    for (int c = 0; c < 5 && !too_small; c++) {
       const int g = cands[c];
       if (occs[c] <= 0) continue;
-      TermParams p;
-      fill_params(pl, fp32, staged, g, 0, p);
-      const uint64_t grid = (uint64_t)ctx->sms * (uint64_t)occs[c];
-      p.total_teams = grid * (uint64_t)teams_per_cta(g);
-      if (p.total_teams > ctx->partial_cap) continue;
-      const uint64_t S = std::min<uint64_t>(pl.T, 2 * p.total_teams);
-      if (S < p.total_teams) {  // fewer terms than teams: too small to tell apart, use the model
-        best_g = model_g;
-        best_per_term = -1.0;
-        break;
-      }
-      p.rounds = (S + p.total_teams - 1) / p.total_teams;
-      p.t_begin = 0;
-      p.t_end = S;
-      // the trial stages its own S terms at stride S (rows x S entries, within the buffer the
-      // caller sized for rows x chunk with S <= chunk)
-      void* stage = staged ? ctx->d_stage : nullptr;
-      const long long stage_ld = staged ? (long long)S : 0;
-      if (staged) {
-        const size_t rows = pl.bord ? 2 * (size_t)pl.h + 1 : (size_t)pl.h;
-        if (rows * S * (fp32 ? sizeof(float2) : sizeof(double2)) > ctx->stage_bytes || S > ctx->wstage_terms) continue;
-      }
-      float ms = 0.f;
-      for (int rep = 0; rep < 2; rep++) {
-        cudaEventRecord(ctx->tev0, ctx->stream);
-        if (launch_terms(fp32, g, chat, p, (int)grid, ctx->d_partials, ctx->stream, stage, ctx->d_wstage, stage_ld) !=
-            cudaSuccess) {
-          cudaGetLastError();
-          ms = -1.f;
+      const int wpc = cta_threads(g) / 32;
+      int occ_bal = occs[c];
+      while (occ_bal > 0 && (occ_bal * wpc) % 4 != 0) occ_bal--;
+      const int trials[2] = {occs[c], (occ_bal > 0 && occ_bal != occs[c] && occ_bal * wpc >= 4) ? occ_bal : 0};
+      for (int o : trials) {
+        if (o <= 0) continue;
+        TermParams p;
+        fill_params(pl, fp32, staged, g, 0, p);
+        const uint64_t grid = (uint64_t)ctx->sms * (uint64_t)o;
+        p.total_teams = grid * (uint64_t)teams_per_cta(g);
+        if (p.total_teams > ctx->partial_cap) continue;
+        const uint64_t S = std::min<uint64_t>(pl.T, 2 * p.total_teams);
+        if (S < p.total_teams) {  // fewer terms than teams: too small to tell apart, use the model
+          best_g = model_g;
+          best_occ = occ_of(model_g);
+          too_small = true;
           break;
         }
-        cudaEventRecord(ctx->tev1, ctx->stream);
-        cudaEventSynchronize(ctx->tev1);
-        cudaEventElapsedTime(&ms, ctx->tev0, ctx->tev1);
-      }
-      if (ms <= 0.f) continue;
-      const double per_term = ms / (double)S;
-      if (per_term < best_per_term) {
-        best_per_term = per_term;
-        best_g = g;
+        p.rounds = (S + p.total_teams - 1) / p.total_teams;
+        p.t_begin = 0;
+        p.t_end = S;
+        // the trial stages its own S terms at stride S (rows x S entries, within the buffer the
+        // caller sized for rows x chunk with S <= chunk)
+        void* stage = staged ? ctx->d_stage : nullptr;
+        const long long stage_ld = staged ? (long long)S : 0;
+        if (staged) {
+          const size_t rows = pl.bord ? 2 * (size_t)pl.h + 1 : (size_t)pl.h;
+          if (rows * S * (fp32 ? sizeof(float2) : sizeof(double2)) > ctx->stage_bytes || S > ctx->wstage_terms)
+            continue;
+        }
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; rep++) {
+          cudaEventRecord(ctx->tev0, ctx->stream);
+          if (launch_terms(fp32, g, chat, p, (int)grid, ctx->d_partials, ctx->stream, stage, ctx->d_wstage,
+                           stage_ld) != cudaSuccess) {
+            cudaGetLastError();
+            ms = -1.f;
+            break;
+          }
+          cudaEventRecord(ctx->tev1, ctx->stream);
+          cudaEventSynchronize(ctx->tev1);
+          cudaEventElapsedTime(&ms, ctx->tev0, ctx->tev1);
+        }
+        if (ms <= 0.f) continue;
+        const double per_term = ms / (double)S;
+        if (per_term < best_per_term) {
+          best_per_term = per_term;
+          best_g = g;
+          best_occ = o;
+        }
       }
     }
   }
-  ctx->tuned[key] = best_g;
-  *ctas_per_sm = occ_of(best_g);
+  ctx->tuned[key] = best_g | (best_occ << 16);
+  *ctas_per_sm = best_occ;
   return best_g;
 }
 
@@ -371,6 +430,7 @@ lhaf_status run_terms(lhaf_ctx* ctx, const Plan& pl, uint32_t flags, uint64_t tb
   const void* chat = fp32 ? (const void*)ctx->d_chat32 : (const void*)ctx->d_chat;
   const int team = pick_team(ctx, fp32, pl, staged, 0, chat, &occ);
   if (team == 0) return LHAF_ETOOBIG;
+  occ = ctas_per_sm_override(occ);
   TermParams p;
   fill_params(pl, fp32, staged, team, flags, p);
   const int tpc = teams_per_cta(team);
@@ -378,16 +438,13 @@ lhaf_status run_terms(lhaf_ctx* ctx, const Plan& pl, uint32_t flags, uint64_t tb
   double* acc_dd = dd_dst ? dd_dst : ctx->d_out;  // running double-double sum over chunks
   if (timed) cudaEventRecord(ctx->ev0, ctx->stream);
   uint64_t c0 = tb;
-  int ci = 0;
+  int ci = 0, launches = 0;
   do {
     const uint64_t c1 = std::min<uint64_t>(te, c0 + chunk);
     const uint64_t n = c1 - c0;
-    uint64_t grid = (n + tpc - 1) / tpc;
-    if (grid > max_ctas) grid = max_ctas;
-    if (grid < 1) grid = 1;
+    const uint64_t grid = balanced_grid(n, tpc, max_ctas, &p.rounds);
     p.total_teams = grid * (uint64_t)tpc;
     if (!staged && p.total_teams > ctx->partial_cap) return LHAF_ETOOBIG;
-    p.rounds = (n + p.total_teams - 1) / p.total_teams;
     p.t_begin = c0;
     p.t_end = c1;
     cudaError_t e;
@@ -397,19 +454,22 @@ lhaf_status run_terms(lhaf_ctx* ctx, const Plan& pl, uint32_t flags, uint64_t tb
     } else if (staged) {
       e = launch_terms(fp32, team, chat, p, (int)grid, ctx->d_partials, ctx->stream, ctx->d_stage, ctx->d_wstage,
                        (long long)chunk);
-      if (const cudaError_t e_ = (e); e_ != cudaSuccess) return (lhaf_status)record_cuda(e_, "e");
+      if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "terms kernel");
       e = launch_series(fp32, ctx->d_stage, ctx->d_wstage, (long long)n, (long long)chunk, pl.h, pl.bord, p.plain,
                         ctx->d_partials, ctx->stream);
-      if (const cudaError_t e_ = (e); e_ != cudaSuccess) return (lhaf_status)record_cuda(e_, "e");
+      if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "series kernel");
       nparts = series_blocks((long long)n);
+      launches += 2;
     } else {
       e = launch_terms(fp32, team, chat, p, (int)grid, ctx->d_partials, ctx->stream);
-      if (const cudaError_t e_ = (e); e_ != cudaSuccess) return (lhaf_status)record_cuda(e_, "e");
+      if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "terms kernel");
       nparts = (long long)p.total_teams;
+      launches += 1;
     }
     const bool last = c1 >= te;
     e = launch_reduce(ctx->d_partials, nparts, pl.h, acc_dd, last ? val_dst : nullptr, ctx->stream, ci > 0 ? 1 : 0);
-    if (const cudaError_t e_ = (e); e_ != cudaSuccess) return (lhaf_status)record_cuda(e_, "e");
+    if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "reduction kernel");
+    launches += 1;
     c0 = c1;
     ci++;
   } while (c0 < te);
@@ -422,6 +482,7 @@ lhaf_status run_terms(lhaf_ctx* ctx, const Plan& pl, uint32_t flags, uint64_t tb
     stats->team = team;
     stats->flops_model = (double)T * lhaf_model_flops_per_term(pl.nd, pl.h, pl.bord);
     stats->kernel_ms = 0.0;
+    stats->launches = launches;
   }
   return LHAF_OK;
 }
@@ -453,11 +514,18 @@ lhaf_status lhaf_common(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c12
     if (st != LHAF_OK) return st;
   }
   if (stats) std::memset(stats, 0, sizeof(*stats));
+  std::vector<Plan> subs;
+  const bool split = pl.N > 0 && !(flags & LHAF_NO_ZERO_SPLIT) && split_zero_digits(pl, subs);
+  uint64_t T_eval = pl.T;
+  if (split) {
+    T_eval = 0;
+    for (const Plan& sp : subs) T_eval += sp.T;
+  }
   if (ranged) {
-    if (tb > te || te > pl.T) return LHAF_EINVAL;
+    if (tb > te || te > T_eval) return LHAF_EINVAL;
   } else {
     tb = 0;
-    te = pl.T;
+    te = T_eval;
   }
   if (pl.N == 0) {  // empty pattern: lhaf = 1 (one empty matching)
     if (ranged) {
@@ -477,16 +545,27 @@ lhaf_status lhaf_common(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c12
     return LHAF_OK;
   }
   const bool fp32 = (flags & LHAF_FP32_TERMS) != 0;
-  st = stage_chat(ctx, pl, M, B, gamma, flags, fp32);
-  if (st != LHAF_OK) return st;
   const bool timed = stats != nullptr;
   double* dd_dst = ranged ? (dev ? partial_dd : ctx->d_out) : nullptr;
   double2* val_dst = ranged ? nullptr : (dev ? (double2*)out : (double2*)(ctx->d_out + 4));
-  st = run_terms(ctx, pl, flags, tb, te, dd_dst, val_dst, stats, timed);
+  if (split) {
+    // zero-digit groups: one persistent launch over all groups' term ranges
+    st = run_split_single(ctx, M, B, gamma, reps, pl.bord ? flags : (flags | LHAF_NO_LOOPS), dev, tb, te, dd_dst,
+                          val_dst, stats);
+  } else {
+    st = stage_chat(ctx, pl, M, B, gamma, flags, fp32);
+    if (st != LHAF_OK) return st;
+    st = run_terms(ctx, pl, flags, tb, te, dd_dst, val_dst, stats, timed);
+    if (st == LHAF_OK && stats) {
+      if (dev) stats->launches += 1;  // slot-matrix gather
+      stats->h2d_bytes = dev ? 0 : (uint64_t)pl.nd * pl.nd * (fp32 ? sizeof(float2) : sizeof(double2));
+    }
+  }
   if (st != LHAF_OK) return st;
+  if (stats) stats->d2h_bytes = dev ? 0 : 6 * sizeof(double);
   if (!dev) {
     cudaError_t e = cudaMemcpyAsync(ctx->h_out, ctx->d_out, 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
-    if (const cudaError_t e_ = (e); e_ != cudaSuccess) return (lhaf_status)record_cuda(e_, "e");
+    if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "result copy");
   }
   if (!dev || timed) {
     if (const cudaError_t e_ = (cudaStreamSynchronize(ctx->stream)); e_ != cudaSuccess) return (lhaf_status)record_cuda(e_, "cudaStreamSynchronize");

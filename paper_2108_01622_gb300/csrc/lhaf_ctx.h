@@ -59,6 +59,23 @@ struct HostBuf {
   }
 };
 
+// Buffers of one batched evaluation: the context's own (lhaf_batched) or a batched plan's, whose
+// captured graph holds these addresses.
+struct BatchWork {
+  DevBuf items, units, queue, next, partials, unit_begin, item_h, chat, chat32, out, stage, wstage, in_B, in_gamma;
+  HostBuf h_items, h_units, h_queue, h_unit_begin, h_item_h, h_chat, h_chat32, h_out, h_in;
+  cudaEvent_t uploaded = nullptr;  // after the last copies that read the pinned buffers above
+  void release() {
+    if (uploaded) cudaEventDestroy(uploaded);
+    uploaded = nullptr;
+    for (DevBuf* b : {&items, &units, &queue, &next, &partials, &unit_begin, &item_h, &chat, &chat32, &out, &stage,
+                      &wstage, &in_B, &in_gamma})
+      b->release();
+    for (HostBuf* b : {&h_items, &h_units, &h_queue, &h_unit_begin, &h_item_h, &h_chat, &h_chat32, &h_out, &h_in})
+      b->release();
+  }
+};
+
 // Autotuning key: precision, staged series, working dimension, La Budde truncation, degree,
 // border, and the kernel family (0 = single loop hafnian, 1 = batched).
 using TuneKey = std::tuple<int, int, int, int, int, int, int>;
@@ -82,10 +99,10 @@ struct lhaf_ctx {
   float2* h_chat32 = nullptr;
   double* h_out = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, tev0 = nullptr, tev1 = nullptr;
-  // batched form
-  DevBuf b_items, b_units, b_queue, b_next, b_partials, b_unit_begin, b_item_h, b_chat, b_chat32, b_out,
-      b_stage, b_wstage, b_gpart, b_gout;
-  HostBuf hb_items, hb_units, hb_queue, hb_unit_begin, hb_item_h, hb_chat, hb_chat32, hb_out, hb_gout;
+  // batched form and adjoint
+  BatchWork bw;
+  DevBuf b_gpart, b_gout;
+  HostBuf hb_gout;
   // measured best team size per problem shape
   std::map<TuneKey, int> tuned;
   std::mutex mu;
@@ -98,4 +115,13 @@ int pick_team(lhaf_ctx* ctx, bool fp32, const Plan& pl, bool staged, int family,
               int* ctas_per_sm);
 // Fill the sieve description of a plan (everything but the term range and the grid).
 void fill_params(const Plan& pl, bool fp32, bool staged, int team, uint32_t flags, TermParams& p);
+int ctas_per_sm_override(int occ);
+// One loop hafnian through the persistent batched kernel over its zero-digit groups, restricted
+// to [tb, te) of the group numbering: the unscaled double-double partial to dd_dst and/or the
+// scaled value to val_dst (device pointers, either may be NULL), ordered on ctx->stream. The caller
+// holds ctx->mu and has validated host inputs.
+lhaf_status run_split_single(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128* gamma, const int32_t* reps,
+                             uint32_t flags, bool dev_inputs, uint64_t tb, uint64_t te, double* dd_dst,
+                             double2* val_dst, lhaf_stats* stats);
+uint64_t balanced_grid(uint64_t n, int tpc, uint64_t max_ctas, unsigned long long* rounds);
 }  // namespace lhafgpu

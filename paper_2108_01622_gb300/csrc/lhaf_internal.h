@@ -22,6 +22,8 @@ struct TermParams {
   int hp;        // index of the pair whose digit is halved
   int hp_even;   // 1 when eta[hp] is even (its middle digit is counted once)
   int plain;     // 1: plain FP64 accumulation instead of double-double
+  unsigned skip_mask;  // bit q: pair q's digits skip the middle one (k = eta/2) of a zero-digit group
+  double wscale;       // constant weight factor of every term (1, or a zero-digit group's factor)
   int n_items;   // push-item table entries: Hl (Hl - 1) / 2
   int team_bytes;   // shared bytes per team
   int items_bytes;  // shared bytes for the item table + 1/k table
@@ -36,6 +38,8 @@ struct TermParams {
 struct BatchItem {
   TermParams p;         // the item's sieve (t_begin/t_end/rounds/total_teams set per unit)
   long long chat_off;   // element offset of the item's slot matrix in the pool
+  int src;              // index of the loop hafnian (its B and gamma) this sieve belongs to
+  int pad;
   int slot_mode[kMaxDim];
 };
 struct BatchUnit {
@@ -83,9 +87,12 @@ cudaError_t launch_batched(bool fp32, int team, const void* chat_pool, const Bat
                            const BatchUnit* units, const int* queue, int n_units, int* next_unit,
                            double* unit_partials, int team_bytes, int items_bytes, int grid,
                            cudaStream_t stream, void* stage = nullptr, double* wstage = nullptr);
+// Per loop hafnian i: double-double sum of the partials of units item_unit_begin[i] ..
+// item_unit_begin[i+1]-1 (teams each), written unscaled to out_dd[4 i ..] and scaled by 2^-h to
+// out[i] (either may be NULL).
 cudaError_t launch_batch_reduce(const double* unit_partials, const int* item_unit_begin,
                                 const int* item_h, int teams, int n_items, double2* out,
-                                cudaStream_t stream);
+                                cudaStream_t stream, double* out_dd = nullptr);
 cudaError_t launch_batch_gather(const double2* B, long long B_stride, const double2* gamma,
                                 long long gamma_stride, int M, const BatchItem* items, int n_items,
                                 double2* chat_pool, float2* chat32_pool, cudaStream_t stream);

@@ -138,6 +138,8 @@ extern "C" lhaf_status lhaf_noalloc(int device, void* cuda_stream, int M, const 
   p.hp = pl.hp;
   p.hp_even = pl.hp_even;
   p.plain = (flags & LHAF_PLAIN_ACCUM) ? 1 : 0;
+  p.skip_mask = 0u;
+  p.wscale = 1.0;
   p.n_items = pl.Hl * (pl.Hl - 1) / 2;
   p.team_bytes = (int)team_shared_bytes(fp32, pl.nd, pl.H, pl.P);
   p.items_bytes =

@@ -79,6 +79,7 @@ lhaf_status build_plan(int M, const int32_t* reps, uint32_t flags, bool loops, P
   pl.slot_mode.resize(2 * pl.P);
   pl.eta.resize(pl.P);
   pl.radix.resize(pl.P);
+  pl.skip.assign(pl.P, 0);
   for (int q = 0; q < pl.P; q++) {
     pl.slot_mode[2 * q] = pairs[q].a;
     pl.slot_mode[2 * q + 1] = pairs[q].b;
@@ -112,6 +113,71 @@ lhaf_status build_plan(int M, const int32_t* reps, uint32_t flags, bool loops, P
   }
   pl.T = Ti;
   return LHAF_OK;
+}
+
+bool split_zero_digits(const Plan& pl, std::vector<Plan>& subs) {
+  subs.clear();
+  std::vector<int> even;
+  for (int q = 0; q < pl.P; q++)
+    if (pl.eta[q] >= 2 && pl.eta[q] % 2 == 0) even.push_back(q);
+  if (even.empty() || even.size() > 20) return false;
+  const int ne = (int)even.size();
+  for (uint32_t zmask = 0; zmask < (1u << ne); zmask++) {
+    std::vector<char> inZ(pl.P, 0);
+    double ws = 1.0;
+    for (int b = 0; b < ne; b++)
+      if (zmask >> b & 1) {
+        const int q = even[b], e = pl.eta[q];
+        inZ[q] = 1;
+        // C(e, e/2) (-1)^(e/2), exact in double for the counts allowed here
+        double c = 1.0;
+        for (int i = 1; i <= e / 2; i++) c = c * (double)(e / 2 + i) / (double)i;
+        ws *= ((e / 2) % 2) ? -c : c;
+      }
+    Plan s;
+    s.M = pl.M;
+    s.N = pl.N;
+    s.h = pl.h;
+    s.H = pl.H;
+    s.bord = pl.bord;
+    s.wscale = ws;
+    for (int q = 0; q < pl.P; q++) {
+      if (inZ[q]) continue;
+      s.slot_mode.push_back(pl.slot_mode[2 * q]);
+      s.slot_mode.push_back(pl.slot_mode[2 * q + 1]);
+      s.eta.push_back(pl.eta[q]);
+      s.skip.push_back(pl.eta[q] % 2 == 0 ? 1 : 0);
+    }
+    s.P = (int)s.eta.size();
+    if (s.P == 0) continue;  // every delta' = 0: f = 0
+    s.nd = 2 * s.P + s.bord;
+    s.Hl = std::min(s.H, s.nd);
+    // halving: the first odd pair (digits k < (eta+1)/2), else the first pair, whose digits
+    // without the middle split into k < eta/2 and their mirror images
+    int hp = -1;
+    for (int q = 0; q < s.P; q++)
+      if (s.eta[q] % 2 == 1) {
+        hp = q;
+        break;
+      }
+    if (hp < 0) hp = 0;
+    s.hp = hp;
+    s.hp_even = 0;
+    s.radix.resize(s.P);
+    uint64_t T = 1;
+    for (int q = 0; q < s.P; q++) {
+      int r = s.eta[q] + 1 - s.skip[q];
+      if (q == hp) {
+        r = (s.eta[q] % 2) ? (s.eta[q] + 1) / 2 : s.eta[q] / 2;
+        s.skip[q] = 0;  // its digits k < eta/2 never reach the middle
+      }
+      s.radix[q] = r;
+      T *= (uint64_t)r;
+    }
+    s.T = T;
+    subs.push_back(std::move(s));
+  }
+  return true;
 }
 
 void build_chat_host(const Plan& pl, int M, const lhaf_c128* B, const lhaf_c128* gamma, std::complex<double>* chat) {
@@ -183,10 +249,12 @@ double model_lane_efficiency(int nd, int Hl, int h, int bord, int G) {
   for (int l = nd - 1; l >= 0; l--) {
     const int deg = nd - l - 1;
     const int E = std::min(deg, Hl - 2);
-    const double np = E >= 0 ? (E + 1.0) * (Hl - 1) - E * (E + 1.0) / 2 : 0.0;
+    const double npe = E >= 0 ? (E + 1.0) * (Hl - 1) - E * (E + 1.0) / 2 : 0.0;
+    const int dmx = std::min(Hl, l + 1);
+    const double npd = dmx >= 2 ? (dmx - 1.0) * (2.0 * Hl - dmx) / 2 : 0.0;
     const double nq = std::min(Hl, nd - l);
     useful += (double)push_items_valid(nd, Hl, l) + nq;
-    slots += rnd(np + nq, G);
+    slots += rnd(std::min(npe, npd) + nq, 2 * G);
   }
   const int SG = std::min(G, 32);
   const double lg = std::log2((double)SG);

@@ -16,14 +16,27 @@ namespace lhafgpu {
 //   the working dimension is nd = 2P + bord, where bord = 1 adds the loop border index 0;
 //   evaluated terms are the mixed-radix numbers over radix[q] (= eta[q] + 1 except the halved
 //   digit of pair hp), T = prod radix.
+// A zero-digit group (split_zero_digits) is a Plan too: skip[q] = 1 removes the middle digit
+// (k = eta/2) from pair q's digits, and every term's weight carries the factor wscale.
 struct Plan {
   int M = 0, N = 0, h = 0, H = 0, Hl = 0, bord = 0, P = 0, nd = 0;
   int hp = 0, hp_even = 0;
-  std::vector<int> slot_mode, eta, radix;
+  std::vector<int> slot_mode, eta, radix, skip;
+  double wscale = 1.0;
   uint64_t T = 0;
 };
 
 lhaf_status build_plan(int M, const int32_t* reps, uint32_t flags, bool loops, Plan& pl);
+
+// Zero-digit groups of a plan. The middle digit k = eta/2 of a pair with even eta gives
+// delta' = 0: both slot columns of C X_delta' (and both loop entries) vanish, and the term equals
+// the one of the matrix with those two slots deleted (every power trace and loop product only sees
+// the remaining slots). Each subset Z of the even pairs is one group: pairs in Z sit at their
+// middle digit (deleted slots, constant weight factor C(eta, eta/2) (-1)^(eta/2)), the other even
+// pairs skip it, odd pairs take every digit. Every group is closed under delta' -> -delta', so each
+// halves exactly on one of its pairs. A group with no pair left contributes nothing (f = 0 for
+// h >= 1) and is dropped. Returns false (subs empty) when the plan has no even pair.
+bool split_zero_digits(const Plan& pl, std::vector<Plan>& subs);
 
 // Bordered slot matrix (nd x nd, row-major): [0][0] = 0; [0][1+s] = [1+s][0] = v_s (gamma of the
 // slot's mode, 1 for the pad); [b+s][b+t] = B[mode(s)][mode(t)] (0 when either is the pad), with B

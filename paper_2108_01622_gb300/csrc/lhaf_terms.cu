@@ -158,13 +158,17 @@ struct TeamScratch {  // small per-team area
 };
 
 // ---------------------------------------------------------------------------------------------
-// CTA tables shared by the teams: the push items (d, e) of La Budde's recurrence sorted by e then
-// d (2 <= d, d + e <= Hl), and 1/k for k <= H + 1.
+// CTA tables shared by the teams: the push items (d, e) of La Budde's recurrence (2 <= d,
+// d + e <= Hl) twice, sorted by e then d (a level's items with e <= E are a prefix) and sorted by d
+// then e (its items with d <= l + 1 are a prefix), and 1/k for k <= H + 1.
 // ---------------------------------------------------------------------------------------------
+__host__ __device__ constexpr int item_table_bytes(int n_items) { return (n_items * 4 + 15) & ~15; }
+
 template <typename R, int CTA>
 __device__ __forceinline__ void build_cta_tables(const TermParams& p, unsigned char* smem) {
   uint16_t* items = reinterpret_cast<uint16_t*>(smem);
-  R* invk = reinterpret_cast<R*>(smem + ((p.n_items * 2 + 15) & ~15));
+  uint16_t* items_d = items + p.n_items;
+  R* invk = reinterpret_cast<R*>(smem + item_table_bytes(p.n_items));
   const int Hl = p.Hl;
   for (int w = threadIdx.x; w < p.n_items; w += CTA) {
     int e = 0, base = 0;
@@ -173,6 +177,13 @@ __device__ __forceinline__ void build_cta_tables(const TermParams& p, unsigned c
       e++;
     }
     items[w] = (uint16_t)(((2 + (w - base)) << 8) | e);
+    int d = 2;
+    base = 0;
+    while (d < Hl && base + (Hl - d + 1) <= w) {
+      base += Hl - d + 1;
+      d++;
+    }
+    items_d[w] = (uint16_t)((d << 8) | (w - base));
   }
   for (int k = threadIdx.x; k <= p.H + 1; k += CTA) invk[k] = k ? (R)1 / (R)k : (R)0;
 }
@@ -322,8 +333,8 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
   const int team = threadIdx.x / G;
   const int lt = threadIdx.x - team * G;
 
-  uint16_t* items = reinterpret_cast<uint16_t*>(smem);
-  R* invk = reinterpret_cast<R*>(smem + ((p.n_items * 2 + 15) & ~15));
+  const uint16_t* items = reinterpret_cast<const uint16_t*>(smem);
+  const R* invk = reinterpret_cast<const R*>(smem + item_table_bytes(p.n_items));
   unsigned char* tb = smem + p.items_bytes + (size_t)team * p.team_bytes;
   V* W = reinterpret_cast<V*>(tb);
   V* Sa = W + nd * ld;  // inline series arrays, H + 2 entries each (absent when staging)
@@ -372,8 +383,9 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
         } else {
           qt = t / st;
         }
-        const int k = (int)(qt % rad);
         const int eta = p.eta[q];
+        int k = (int)(qt % rad);
+        if (((p.skip_mask >> q) & 1u) && 2 * k >= eta) k++;  // zero-digit group: no middle digit
         wq *= binom_d(eta, k);
         par ^= (k & 1);
         ts->delta[q] = eta - 2 * k;
@@ -384,7 +396,7 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
         wq *= __shfl_xor_sync(0xffffffffu, wq, off);
         par ^= __shfl_xor_sync(0xffffffffu, par, off);
       }
-      if (lt == 0) ts->weight = valid ? (par ? -wq : wq) : 0.0;
+      if (lt == 0) ts->weight = valid ? (par ? -wq : wq) * p.wscale : 0.0;
     }
     team_sync<G>();
 
@@ -587,7 +599,13 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
     for (int l = nd - 1; l >= 0; l--) {
       const int deg = nd - l - 1;  // degree of q_{l+1}
       const int E = min(deg, Hl - 2);
-      const int np = (E >= 0) ? (E + 1) * (Hl - 1) - E * (E + 1) / 2 : 0;
+      // valid pushes have e <= E and d <= l + 1: walk the shorter of the two sorted prefixes
+      const int npe = (E >= 0) ? (E + 1) * (Hl - 1) - E * (E + 1) / 2 : 0;
+      const int dmx = min(Hl, l + 1);
+      const int npd = (dmx >= 2) ? (dmx - 1) * (2 * Hl - dmx) / 2 : 0;
+      const bool by_d = npd < npe;
+      const uint16_t* tab = by_d ? items + p.n_items : items;
+      const int np = by_d ? npd : npe;
       const int nq = min(Hl, nd - l);
       // Every item is dst <- a - b c: a push into acc_j, or the update of q_l[m]. Two items per
       // lane per pass, loads first.
@@ -605,10 +623,10 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
           c[u] = zero;
           if (x < np) {
             // push q_{l+1} into the accumulator of q_j, j = l - d + 1
-            const int it = items[x];
+            const int it = tab[x];
             const int d = it >> 8, e = it & 255;
             const int j = l - d + 1;
-            if (j >= 0) {
+            if (j >= 0 && e <= E) {
               ok[u] = true;
               dst[u] = W + (l + e) * ld + j;
               a[u] = *dst[u];
@@ -941,7 +959,8 @@ batched_kernel(const typename Cx<R>::t* __restrict__ chat_pool, const BatchItem*
 // h < 0 marks an empty pattern (lhaf = 1); h == INT_MAX marks an item that was not computed.
 __global__ void __launch_bounds__(128)
 batch_reduce_kernel(const double* __restrict__ unit_partials, const int* __restrict__ item_unit_begin,
-                    const int* __restrict__ item_h, int teams, int n_items, double2* __restrict__ out) {
+                    const int* __restrict__ item_h, int teams, int n_items, double2* __restrict__ out,
+                    double* __restrict__ out_dd) {
   const int item = blockIdx.x * 4 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (item >= n_items) return;
@@ -960,13 +979,23 @@ batch_reduce_kernel(const double* __restrict__ unit_partials, const int* __restr
   }
   if (lane == 0) {
     const int h = item_h[item];
-    if (h < 0) {
-      out[item] = make_double2(1.0, 0.0);
-    } else if (h == 0x7fffffff) {
-      out[item] = make_double2(__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll));
-    } else {
-      const double s1 = __longlong_as_double((long long)(1023 - h) << 52);
-      out[item] = make_double2((rh + rl) * s1, (ih + il) * s1);
+    if (out_dd) {
+      double* o = out_dd + 4ll * item;
+      o[0] = rh;
+      o[1] = rl;
+      o[2] = ih;
+      o[3] = il;
+    }
+    if (out) {
+      if (h < 0) {
+        out[item] = make_double2(1.0, 0.0);
+      } else if (h == 0x7fffffff) {
+        out[item] =
+            make_double2(__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll));
+      } else {
+        const double s1 = __longlong_as_double((long long)(1023 - h) << 52);
+        out[item] = make_double2((rh + rl) * s1, (ih + il) * s1);
+      }
     }
   }
 }
@@ -980,8 +1009,8 @@ __global__ void batch_gather_kernel(const double2* __restrict__ B, long long B_s
   const BatchItem& it = items[item];
   const int nd = it.p.nd, bord = it.p.bord;
   if (nd <= 0) return;
-  const double2* Bi = B + (long long)item * B_stride;
-  const double2* gi = gamma ? gamma + (long long)item * gamma_stride : nullptr;
+  const double2* Bi = B + (long long)it.src * B_stride;
+  const double2* gi = gamma ? gamma + (long long)it.src * gamma_stride : nullptr;
   for (int w = threadIdx.x; w < nd * nd; w += blockDim.x) {
     const int i = w / nd, j = w - i * nd;
     double2 c = make_double2(0.0, 0.0);
@@ -1239,7 +1268,7 @@ size_t team_shared_bytes(bool fp32, int nd, int H, int P, bool staged) {
 
 static size_t items_bytes_of(bool fp32, int Hl, int H) {
   const int n_items = Hl * (Hl - 1) / 2;
-  size_t b = ((size_t)n_items * 2 + 15) & ~(size_t)15;
+  size_t b = (size_t)item_table_bytes(n_items);
   b += (size_t)(H + 2) * (fp32 ? sizeof(float) : sizeof(double));
   return (b + 15) & ~(size_t)15;
 }
@@ -1420,10 +1449,10 @@ cudaError_t launch_batched(bool fp32, int team, const void* chat_pool, const Bat
 }
 
 cudaError_t launch_batch_reduce(const double* unit_partials, const int* item_unit_begin, const int* item_h, int teams,
-                                int n_items, double2* out, cudaStream_t stream) {
+                                int n_items, double2* out, cudaStream_t stream, double* out_dd) {
   if (n_items <= 0) return cudaSuccess;
   batch_reduce_kernel<<<(n_items + 3) / 4, 128, 0, stream>>>(unit_partials, item_unit_begin, item_h, teams, n_items,
-                                                             out);
+                                                             out, out_dd);
   return cudaGetLastError();
 }
 

@@ -38,6 +38,25 @@ def halved_count(reps, loops):
     return (T // (emax + 1)) * (emax // 2 + 1)
 
 
+def split_count(reps):
+    """Evaluated terms of the zero-digit groups: for every subset Z of the even-eta pairs, the pairs
+    in Z sit at their middle digit (slots deleted), the other even pairs skip it (eta digits), odd
+    pairs take eta + 1 digits; each group is halved once; a group without pairs is dropped."""
+    pairs, leftover = lo.matched_reps(reps)
+    etas = [e for _, _, e in pairs] + ([1] if leftover is not None else [])
+    even = [e for e in etas if e >= 2 and e % 2 == 0]
+    odd = [e for e in etas if e % 2]
+    if not even:
+        return halved_count(reps, True)
+    total = 0
+    for z in itertools.product([0, 1], repeat=len(even)):
+        kept = [e for e, zi in zip(even, z) if not zi]
+        if not kept and not odd:
+            continue
+        total += math.prod(e for e in kept) * math.prod(e + 1 for e in odd) // 2
+    return total
+
+
 @pytest.mark.parametrize("reps", list(itertools.product(range(4), repeat=3)) + [(2, 1, 0, 3), (1,) * 24, (4, 4, 4), (9,)])
 def test_plan_matches_oracle_greedy(lg, reps):
     T, nd, h, P = lg.plan(reps, has_loops=True)
@@ -49,7 +68,8 @@ def test_plan_matches_oracle_greedy(lg, reps):
     assert P == len(pairs) + (leftover is not None)
     assert h == (N + 1) // 2
     assert nd == 2 * P + 1
-    assert T == halved_count(reps, True)
+    assert T == split_count(reps)
+    assert lg.plan(reps, flags=lg.NO_ZERO_SPLIT, has_loops=True)[0] == halved_count(reps, True)
     # without loops the border disappears unless a pad is needed
     T0, nd0, _, _ = lg.plan(reps, has_loops=False)
     assert T0 == T
@@ -60,6 +80,26 @@ def test_worked_example_halved(lg):
     # App. B.2 example n = (2,1,0,3): 6 terms, 3 after the sign-symmetry halving
     T, nd, h, P = lg.plan([2, 1, 0, 3], has_loops=False)
     assert (T, P, h) == (3, 2, 3)
+
+
+def test_plan_groups_count(lg):
+    # pairs [2, 1] (worked example): one even pair -> 2 groups; no even pair -> no split
+    assert lg.plan_groups([2, 1, 0, 3]) == 2
+    assert lg.plan_groups([1, 1, 1, 1]) == 0
+    assert lg.plan_groups([2, 1, 0, 3], flags=lg.NO_ZERO_SPLIT) == 0
+    # (4,): one pair with eta = 2 alone: the group with it at the middle digit is empty (dropped)
+    assert lg.plan_groups([4]) == 1 and lg.plan([4])[0] == 1
+
+
+def test_zero_digit_groups_cover_every_digit_vector():
+    # every digit vector lies in exactly one group: middle digits of the even pairs pick the group
+    for etas in ([2], [2, 2], [4, 1, 2], [3, 2, 2, 1], [6, 4]):
+        even = [e for e in etas if e % 2 == 0]
+        covered = 0
+        for z in itertools.product([0, 1], repeat=len(even)):
+            kept = [e for e, zi in zip(even, z) if not zi]
+            covered += math.prod(kept) * math.prod(e + 1 for e in etas if e % 2)
+        assert covered == math.prod(e + 1 for e in etas)
 
 
 def test_no_repeat_speedup_gives_duplicated_count(lg):
@@ -98,3 +138,15 @@ def test_ctx_create_without_gpu_fails_cleanly(lg):
     with pytest.raises(lg.LhafError) as e:
         lg.Context(0)
     assert e.value.status == 3
+
+
+def test_batched_plan_rejects_bad_arguments_without_a_context(lg):
+    lib = lg._lib()
+    h = ctypes.c_void_p(123)
+    B = np.zeros((2, 2), np.complex128)
+    R = np.ones((1, 2), np.int32)
+    st = lib.lhaf_batched_plan_create(None, 1, 2, B.ctypes.data, None, R.ctypes.data, 0, ctypes.byref(h))
+    assert st == 1 and h.value is None
+    assert lib.lhaf_batched_plan_create(None, 1, 2, B.ctypes.data, None, R.ctypes.data, 0, None) == 1
+    assert lib.lhaf_batched_plan_exec(None, B.ctypes.data, None, B.ctypes.data, None, None) == 1
+    lib.lhaf_batched_plan_destroy(None)

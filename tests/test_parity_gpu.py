@@ -157,15 +157,63 @@ def test_plain_accumulation_close(ctx):
     assert rel(b, a) < 1e-11
 
 
-def test_staging_reuse_with_more_coefficient_rows(ctx):
+@pytest.mark.parametrize("seed,loops", [(21, False), (22, True), (23, True)])
+def test_zero_digit_groups_match_full_matrix_and_oracle(ctx, lg, seed, loops):
+    # collision patterns (counts 1..4): pairs with even eta run as zero-digit groups by default
+    p = wl.collision_lhaf_40(seed=seed, n_modes=9, n_photons=19 if loops else 18)
+    if loops:
+        p.gamma = wl.complex_normal(np.random.default_rng(seed), len(p.gamma))
+    ref = lo.lhaf_repeated(p.B, p.gamma, p.reps)
+    split, st = ctx.lhaf(p.B, p.gamma, p.reps, stats=True)
+    full, st0 = ctx.lhaf(p.B, p.gamma, p.reps, flags=lg.NO_ZERO_SPLIT, stats=True)
+    assert st["terms"] == lg.plan(p.reps)[0] and st0["terms"] == lg.plan(p.reps, flags=lg.NO_ZERO_SPLIT)[0]
+    assert rel(split, ref) < TOL and rel(full, ref) < TOL
+    assert st["flops_model"] < st0["flops_model"]
+
+
+def test_zero_digit_range_partials_cross_groups(ctx, lg):
+    p = wl.collision_lhaf_40(seed=12, n_modes=8, n_photons=16)
+    p.gamma = wl.complex_normal(np.random.default_rng(3), len(p.gamma))
+    T, nd, h, P = lg.plan(p.reps)
+    full = ctx.lhaf(p.B, p.gamma, p.reps)
+    cuts = sorted({0, 1, 3, T // 5, T // 3, T // 2 + 1, T - 1, T})
+    parts = [ctx.lhaf_range(p.B, p.gamma, p.reps, a, b) for a, b in zip(cuts[:-1], cuts[1:])]
+    assert rel(lg.combine(np.array(parts), h), full) < 1e-13
+    assert rel(full, lo.lhaf_repeated(p.B, p.gamma, p.reps)) < TOL
+    with pytest.raises(lg.LhafError):
+        ctx.lhaf_range(p.B, p.gamma, p.reps, 0, T + 1)
+
+
+def test_zero_digit_groups_device_pointers_and_fp32(ctx, lg):
+    import torch
+
+    p = wl.collision_lhaf_40(seed=31, n_modes=10, n_photons=22)
+    ref = lo.lhaf_repeated(p.B, p.gamma, p.reps)
+    Bd = torch.from_numpy(p.B).cuda()
+    gd = torch.from_numpy(p.gamma).cuda()
+    out = ctx.lhaf(Bd, gd, p.reps, flags=lg.NO_LOOPS)
+    torch.cuda.synchronize()
+    assert rel(complex(out.cpu()[0]), ref) < TOL
+    out = ctx.lhaf(Bd, gd, p.reps)  # loop border kept (gamma = 0 on the device is not inspected)
+    torch.cuda.synchronize()
+    assert rel(complex(out.cpu()[0]), ref) < TOL
+    assert rel(ctx.lhaf(p.B, p.gamma, p.reps, flags=lg.FP32_TERMS), ref) < 1e-3
+
+
+@pytest.mark.parametrize("flags", [0, 0x40])
+def test_staging_reuse_with_more_coefficient_rows(ctx, flags):
+    _staging_reuse(ctx, flags)
+
+
+def _staging_reuse(ctx, flags):
     # A staged call with many terms and few coefficient rows, then a new problem shape with more
     # rows and few terms (autotuned on its first call): both must match the oracle.
     p1 = wl.collision_lhaf_40(seed=2)  # no loops: h = 20 rows, 34,560 terms
-    assert rel(ctx.lhaf(p1.B, p1.gamma, p1.reps), lo.lhaf_repeated(p1.B, p1.gamma, p1.reps)) < TOL
+    assert rel(ctx.lhaf(p1.B, p1.gamma, p1.reps, flags=flags), lo.lhaf_repeated(p1.B, p1.gamma, p1.reps)) < TOL
     b = wl.chain_rule_batch(seed=3, count=64)
     for i in range(len(b.reps)):
         r = b.reps[i]
         if 30 <= r.sum() <= 34:  # loops: 2h + 1 rows
-            got = ctx.lhaf(b.B, b.gammas[i], r)
+            got = ctx.lhaf(b.B, b.gammas[i], r, flags=flags)
             assert rel(got, lo.lhaf_repeated(b.B, b.gammas[i], r)) < TOL
             break
