@@ -65,6 +65,7 @@ extern "C" void lhaf_ctx_destroy(lhaf_ctx* ctx) {
   if (ctx->tev0) cudaEventDestroy(ctx->tev0);
   if (ctx->tev1) cudaEventDestroy(ctx->tev1);
   ctx->bw.release();
+  ctx->gw.release();
   ctx->b_gpart.release();
   ctx->b_gout.release();
   ctx->hb_gout.release();
@@ -385,7 +386,9 @@ lhaf_status validate_host_inputs(int M, const lhaf_c128* B, const lhaf_c128* gam
 // Staging buffer for the series kernel: grown on demand (terms x coefficient rows).
 constexpr size_t kStageBytesMax = (size_t)256 << 20;
 
-bool ensure_stage(lhaf_ctx* ctx, size_t bytes, size_t terms) {
+}  // namespace
+
+bool lhafgpu::ensure_stage(lhaf_ctx* ctx, size_t bytes, size_t terms) {
   if (ctx->stage_bytes >= bytes && ctx->wstage_terms >= terms) return true;
   cudaStreamSynchronize(ctx->stream);
   cudaFree(ctx->d_stage);
@@ -403,6 +406,8 @@ bool ensure_stage(lhaf_ctx* ctx, size_t bytes, size_t terms) {
   ctx->wstage_terms = terms;
   return true;
 }
+
+namespace {
 
 // Runs the sieve over [tb, te) of the plan; writes the dd partial (unscaled) and/or the scaled
 // value into device buffers dd_dst / val_dst. Degrees up to kStageMaxDegree stage the term
@@ -487,6 +492,188 @@ lhaf_status run_terms(lhaf_ctx* ctx, const Plan& pl, uint32_t flags, uint64_t tb
   return LHAF_OK;
 }
 
+// One loop hafnian over its zero-digit groups `subs` (numbered group after group), restricted to
+// [tb, te): grid-strided chunks that never straddle two groups (grouped_terms_kernel), then, for
+// degrees up to kStageMaxDegree, the staged series one term per thread; both in launches sized to
+// the staging buffer. Writes the unscaled dd partial to dd_dst and/or the value to val_dst.
+lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& subs, int M, const lhaf_c128* B,
+                        const lhaf_c128* gamma, uint32_t flags, bool dev, uint64_t tb, uint64_t te, double* dd_dst,
+                        double2* val_dst, lhaf_stats* stats, bool timed) {
+  const bool fp32 = (flags & LHAF_FP32_TERMS) != 0;
+  const char* env_stage = std::getenv("LHAF_STAGE");
+  bool staged = pl.h <= kStageMaxDegree && !(env_stage && env_stage[0] == '0');
+  const size_t cs = fp32 ? sizeof(float2) : sizeof(double2);
+  const int rows = pl.bord ? 2 * pl.h + 1 : pl.h;
+  BatchWork& w = ctx->gw;
+  cudaStream_t s = ctx->stream;
+  // the previous call's uploads read the pinned buffers rewritten below
+  if (w.uploaded) {
+    if (const cudaError_t e = cudaEventSynchronize(w.uploaded); e != cudaSuccess)
+      return (lhaf_status)record_cuda(e, "cudaEventSynchronize");
+  } else if (cudaEventCreateWithFlags(&w.uploaded, cudaEventDisableTiming) != cudaSuccess) {
+    w.uploaded = nullptr;
+    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "cudaEventCreate");
+  }
+  const int nj = (int)subs.size();
+  if (!w.h_items.reserve(sizeof(BatchItem) * nj) || !w.items.reserve(sizeof(BatchItem) * nj) ||
+      !w.h_chunks.reserve(sizeof(long long) * (nj + 1)) || !w.chunks.reserve(sizeof(long long) * (nj + 1)))
+    return LHAF_ENOMEM;
+  BatchItem* jobs = static_cast<BatchItem*>(w.h_items.p);
+  std::memset(jobs, 0, sizeof(BatchItem) * nj);
+  long long pool = 0;
+  int nd_max = 0, P_max = 0, Hl_max = 0, rep = 0;
+  double cost_max = -1.0;
+  uint64_t base = 0;
+  std::vector<uint64_t> bases(nj);
+  for (int j = 0; j < nj; j++) {
+    const Plan& sp = subs[j];
+    fill_params(sp, fp32, staged, 32, flags, jobs[j].p);
+    jobs[j].p.t_end = sp.T;  // the sieve's term count (the kernel sets the per-chunk range)
+    jobs[j].chat_off = pool;
+    jobs[j].base = base;
+    jobs[j].src = 0;
+    for (int q = 0; q < kMaxDim; q++) jobs[j].slot_mode[q] = q < 2 * sp.P ? sp.slot_mode[q] : -1;
+    bases[j] = base;
+    base += sp.T;
+    pool += (long long)sp.nd * sp.nd;
+    nd_max = std::max(nd_max, sp.nd);
+    P_max = std::max(P_max, sp.P);
+    Hl_max = std::max(Hl_max, sp.Hl);
+    const double c = lhaf_model_flops_per_term(sp.nd, sp.h, sp.bord) * (double)sp.T;
+    if (c > cost_max) {
+      cost_max = c;
+      rep = j;
+    }
+  }
+  if (!w.chat.reserve(sizeof(double2) * std::max<long long>(pool, 1)) ||
+      (fp32 && !w.chat32.reserve(sizeof(float2) * std::max<long long>(pool, 1))))
+    return LHAF_ENOMEM;
+  uint64_t h2d = sizeof(BatchItem) * (uint64_t)nj;
+  int launches = 0;
+  if (cudaMemcpyAsync(w.items.p, jobs, sizeof(BatchItem) * nj, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "group descriptors");
+  if (dev) {
+    if (launch_batch_gather((const double2*)B, 0, (const double2*)gamma, 0, M, (const BatchItem*)w.items.p, nj,
+                            (double2*)w.chat.p, fp32 ? (float2*)w.chat32.p : nullptr, s) != cudaSuccess)
+      return (lhaf_status)record_cuda(cudaPeekAtLastError(), "group slot-matrix gather");
+    launches++;
+  } else {
+    if (!w.h_chat.reserve(sizeof(double2) * std::max<long long>(pool, 1))) return LHAF_ENOMEM;
+    std::complex<double>* hc = static_cast<std::complex<double>*>(w.h_chat.p);
+    for (int j = 0; j < nj; j++) build_chat_host(subs[j], M, B, gamma, hc + jobs[j].chat_off);
+    if (fp32) {
+      if (!w.h_chat32.reserve(sizeof(float2) * std::max<long long>(pool, 1))) return LHAF_ENOMEM;
+      float2* h32 = static_cast<float2*>(w.h_chat32.p);
+      for (long long e = 0; e < pool; e++) h32[e] = make_float2((float)hc[e].real(), (float)hc[e].imag());
+      if (cudaMemcpyAsync(w.chat32.p, h32, sizeof(float2) * pool, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return (lhaf_status)record_cuda(cudaPeekAtLastError(), "group slot matrices");
+    } else if (cudaMemcpyAsync(w.chat.p, hc, sizeof(double2) * pool, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      return (lhaf_status)record_cuda(cudaPeekAtLastError(), "group slot matrices");
+    }
+    h2d += (uint64_t)pool * cs;
+  }
+  // staging buffer first: the tuner's staged trial writes into it
+  const uint64_t T_all = base;
+  uint64_t cap_cols = 0;
+  if (staged) {
+    cap_cols = kStageBytesMax / ((size_t)rows * cs);
+    cap_cols = std::min<uint64_t>(cap_cols, (uint64_t)ctx->partial_cap * 64);  // series blocks of 64 terms
+    cap_cols = std::min<uint64_t>(cap_cols, T_all + 128 * (uint64_t)nj);     // at most every term plus padding
+    if (!ensure_stage(ctx, (size_t)rows * cs * cap_cols, cap_cols)) staged = false;
+  }
+  const void* pool_ptr = fp32 ? w.chat32.p : w.chat.p;
+  int occ = 0;
+  const char* chatp = static_cast<const char*>(pool_ptr) + (size_t)jobs[rep].chat_off * cs;
+  const int team = pick_team(ctx, fp32, subs[rep], staged, 2, chatp, &occ);
+  if (team == 0) return LHAF_ETOOBIG;
+  const int tpc = teams_per_cta(team);
+  if (staged && cap_cols < (uint64_t)tpc) return LHAF_ETOOBIG;  // a launch stages whole chunks
+  const size_t team_bytes = team_shared_bytes(fp32, nd_max, pl.H, P_max, staged);
+  const size_t items_bytes = cta_table_bytes(fp32, Hl_max, pl.H);
+  const size_t smem = items_bytes + (size_t)tpc * team_bytes;
+  if (smem > 227 * 1024) return LHAF_ETOOBIG;
+  const int occ_g = grouped_ctas_per_sm(fp32, team, smem, staged);
+  if (occ_g <= 0) return LHAF_ETOOBIG;
+  occ = ctas_per_sm_override(std::min(occ > 0 ? occ : occ_g, occ_g));
+  // chunks of tpc terms per group, and the chunk range covering [tb, te)
+  std::vector<long long> chunk_off(nj + 1, 0);
+  for (int j = 0; j < nj; j++) chunk_off[j + 1] = chunk_off[j] + (long long)((subs[j].T + tpc - 1) / tpc);
+  auto chunk_of = [&](uint64_t t) -> long long {  // chunk holding term t (t < T_all)
+    int j = 0;
+    while (j + 1 < nj && bases[j + 1] <= t) j++;
+    return chunk_off[j] + (long long)((t - bases[j]) / tpc);
+  };
+  long long kb = 0, ke = 0;
+  if (te > tb) {
+    kb = chunk_of(tb);
+    ke = chunk_of(te - 1) + 1;
+  }
+  long long* hco = static_cast<long long*>(w.h_chunks.p);
+  std::memcpy(hco, chunk_off.data(), sizeof(long long) * (nj + 1));
+  if (cudaMemcpyAsync(w.chunks.p, hco, sizeof(long long) * (nj + 1), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "group chunk offsets");
+  h2d += sizeof(long long) * (uint64_t)(nj + 1);
+  if (cudaEventRecord(w.uploaded, s) != cudaSuccess)
+    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "cudaEventRecord");
+
+  const uint64_t max_ctas = (uint64_t)ctx->sms * (uint64_t)occ;
+  double* acc_dd = dd_dst ? dd_dst : ctx->d_out;
+  if (timed) cudaEventRecord(ctx->ev0, s);
+  const long long span = staged ? std::max<long long>(1, (long long)(cap_cols / tpc)) : (ke - kb);
+  long long c0 = kb;
+  int ci = 0;
+  do {
+    const long long c1 = std::min<long long>(ke, c0 + std::max<long long>(span, 1));
+    const long long n = c1 - c0;  // chunks in this launch
+    long long nparts = 0;
+    if (n > 0) {
+      unsigned long long rounds = 1;
+      const uint64_t grid = balanced_grid((uint64_t)n, 1, max_ctas, &rounds);
+      if (!staged && grid * (uint64_t)tpc > ctx->partial_cap) return LHAF_ETOOBIG;
+      cudaError_t e = launch_grouped_terms(fp32, team, pool_ptr, (const BatchItem*)w.items.p, nj,
+                                           (const long long*)w.chunks.p, c0, c1, (int)grid, (int)rounds, tb, te,
+                                           (int)team_bytes, (int)items_bytes, ctx->d_partials,
+                                           staged ? ctx->d_stage : nullptr, staged ? ctx->d_wstage : nullptr,
+                                           staged ? (long long)cap_cols : 0, s);
+      if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "grouped terms kernel");
+      launches++;
+      if (staged) {
+        e = launch_series(fp32, ctx->d_stage, ctx->d_wstage, n * tpc, (long long)cap_cols, pl.h, pl.bord,
+                          (flags & LHAF_PLAIN_ACCUM) ? 1 : 0, ctx->d_partials, s);
+        if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "series kernel");
+        launches++;
+        nparts = series_blocks(n * tpc);
+      } else {
+        nparts = (long long)grid * tpc;
+      }
+    }
+    const bool last = c1 >= ke;
+    cudaError_t e = launch_reduce(ctx->d_partials, nparts, pl.h, acc_dd, last ? val_dst : nullptr, s, ci > 0 ? 1 : 0);
+    if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "reduction kernel");
+    launches++;
+    c0 = c1;
+    ci++;
+  } while (c0 < ke);
+  if (timed) cudaEventRecord(ctx->ev1, s);
+  if (stats) {
+    double flops = 0.0;
+    for (int j = 0; j < nj; j++) {
+      const uint64_t lo = std::max<uint64_t>(tb, bases[j]), hi = std::min<uint64_t>(te, bases[j] + subs[j].T);
+      if (hi > lo) flops += (double)(hi - lo) * lhaf_model_flops_per_term(subs[j].nd, subs[j].h, subs[j].bord);
+    }
+    stats->terms = te - tb;
+    stats->n_dim = nd_max;
+    stats->h = pl.h;
+    stats->pairs = pl.P;
+    stats->team = team;
+    stats->flops_model = flops;
+    stats->kernel_ms = 0.0;
+    stats->launches = launches;
+    stats->h2d_bytes = h2d;
+  }
+  return LHAF_OK;
+}
+
 lhaf_status lhaf_common(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128* gamma, const int32_t* reps,
                         uint32_t flags, bool ranged, uint64_t tb, uint64_t te, lhaf_c128* out, double* partial_dd,
                         lhaf_stats* stats) {
@@ -549,9 +736,7 @@ lhaf_status lhaf_common(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c12
   double* dd_dst = ranged ? (dev ? partial_dd : ctx->d_out) : nullptr;
   double2* val_dst = ranged ? nullptr : (dev ? (double2*)out : (double2*)(ctx->d_out + 4));
   if (split) {
-    // zero-digit groups: one persistent launch over all groups' term ranges
-    st = run_split_single(ctx, M, B, gamma, reps, pl.bord ? flags : (flags | LHAF_NO_LOOPS), dev, tb, te, dd_dst,
-                          val_dst, stats);
+    st = run_grouped(ctx, pl, subs, M, B, gamma, flags, dev, tb, te, dd_dst, val_dst, stats, timed);
   } else {
     st = stage_chat(ctx, pl, M, B, gamma, flags, fp32);
     if (st != LHAF_OK) return st;

@@ -1,6 +1,14 @@
-// Batched loop hafnians (the chain-rule sampler's conditional probabilities, App. A.2 and
-// App. B.5): many lhaf(B_n) of uneven size in one persistent launch, either planned per call
+// Batched loop hafnians (the chain-rule sampler's conditional probabilities, App. A.2, and the
+// batching motivation of App. B.5): many lhaf(B_n) of uneven size, planned per call
 // (lhaf_batched) or planned once and replayed from a captured CUDA graph (lhaf_batched_plan_*).
+//
+// Every item becomes one sieve, or its zero-digit groups (several smaller sieves). Sieves are
+// sorted into classes by series mode (staged for degrees up to kStageMaxDegree, inline above) and
+// working dimension, so each class gets its own team size, shared-memory layout and occupancy.
+// A class runs as grouped terms launches (grid-strided chunks that never straddle two sieves) over
+// chunk ranges sized to a staging budget; each launch ends in per-column values (the staged series,
+// one term per thread, or the teams' per-chunk partials) that a segmented reduction adds to each
+// item's double-double accumulator. A last kernel scales by 2^-h per item.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -11,7 +19,6 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
-#include <numeric>
 #include <vector>
 
 #include "../../include/lhaf.h"
@@ -25,19 +32,46 @@ namespace {
 
 bool finite_c(const lhaf_c128& z) { return std::isfinite(z.re) && std::isfinite(z.im); }
 
+// Per-launch budget of staged coefficient rows (staged classes) or per-chunk partials (inline).
+constexpr size_t kLaunchBytes = (size_t)192 << 20;
+
+// Working-dimension class bounds: a class holds the sieves with nd in (previous bound, bound].
+constexpr int kClassBounds[] = {8, 12, 16, 20, 24, 28, 32, 40, 48, 64};
+constexpr int kNumBounds = (int)(sizeof(kClassBounds) / sizeof(kClassBounds[0]));
+
+struct GLaunch {
+  long long c0 = 0, c1 = 0;  // chunk range of the class
+  int grid = 0, rounds = 0;
+  long long sb_off = 0;      // first of its n_seg + 1 segment boundaries
+  long long si_off = 0;      // first of its n_seg segment items
+  int n_seg = 0;
+};
+
+struct GClass {
+  bool staged = false;
+  int team = 0, tpc = 1;
+  int team_bytes = 0, items_bytes = 0;
+  int h_max = 0, rows_max = 0;
+  long long desc_off = 0;   // first descriptor of the class
+  long long chunk_off = 0;  // first of its n_jobs + 1 chunk offsets
+  int n_jobs = 0;
+  long long cols_cap = 0;   // columns one launch stages (row stride of the staging buffer)
+  std::vector<GLaunch> launches;
+};
+
 // Everything the launches of one planned batch need.
 struct BatchLaunch {
   int batch = 0, M = 0;
   bool fp32 = false;
-  int team = 0, teams = 1, team_bytes = 0, items_bytes = 0, grid = 0, n_units = 0;
-  long long region_elems = 0;
   long long B_stride = 0;
-  int n_desc = 0;  // sieve descriptors (items, or their zero-digit groups)
-  uint64_t h2d = 0;  // bytes planning copied host -> device
+  int n_desc = 0;
+  int plain = 0;
+  std::vector<GClass> classes;
+  uint64_t h2d = 0;       // bytes planning copied host -> device
   int prep_launches = 0;  // kernels planning launched (the slot-matrix gather)
   uint64_t terms = 0;
   double flops = 0.0;
-  int nd_max = 0, h_max = 0;
+  int nd_max = 0, h_max = 0, team = 0;
 };
 
 // Validity of the host entries item i reads (its occupied rows and columns of B, its gamma).
@@ -52,20 +86,21 @@ lhaf_status validate_item(int M, const int32_t* r, const lhaf_c128* Bi, const lh
   return LHAF_OK;
 }
 
-// Host planning of a batch into the buffers w: per-item plans and status, descriptors, the
-// slot-matrix pool (built on the host from host inputs, or gathered on the device from device
-// inputs), the team size (tuned on the costliest item), the work units and their queue. All
-// uploads are ordered on the context's stream. B and gamma are host pointers unless dev_inputs.
+// Host planning of a batch into the buffers w: per-item plans and status, the sieves (zero-digit
+// groups unless LHAF_NO_ZERO_SPLIT), their descriptors and slot matrices (built on the host from
+// host inputs, or gathered on the device from device inputs), the classes with their tuned team
+// sizes, and every launch's chunk range and item segments. All uploads are ordered on the
+// context's stream. B and gamma are host pointers unless dev_inputs.
 lhaf_status prepare_batch(lhaf_ctx* ctx, BatchWork& w, int batch, int M, const lhaf_c128* B,
                           const lhaf_c128* gamma, const int32_t* reps, uint32_t flags, bool dev_inputs,
-                          std::vector<lhaf_status>& st, BatchLaunch& L, uint64_t range_tb = 0,
-                          uint64_t range_te = UINT64_MAX) {
+                          std::vector<lhaf_status>& st, BatchLaunch& L) {
   const bool per_item_B = (flags & LHAF_BATCH_B_PER_ITEM) != 0;
   const bool fp32 = (flags & LHAF_FP32_TERMS) != 0;
+  const size_t cs = fp32 ? sizeof(float2) : sizeof(double2);
   // the previous planning's uploads read the pinned buffers rewritten below: let them finish
   if (w.uploaded) {
-    if (const cudaError_t e_ = cudaEventSynchronize(w.uploaded); e_ != cudaSuccess)
-      return (lhaf_status)record_cuda(e_, "cudaEventSynchronize");
+    if (const cudaError_t e = cudaEventSynchronize(w.uploaded); e != cudaSuccess)
+      return (lhaf_status)record_cuda(e, "cudaEventSynchronize");
   } else if (cudaEventCreateWithFlags(&w.uploaded, cudaEventDisableTiming) != cudaSuccess) {
     w.uploaded = nullptr;
     return (lhaf_status)record_cuda(cudaPeekAtLastError(), "cudaEventCreate");
@@ -74,6 +109,7 @@ lhaf_status prepare_batch(lhaf_ctx* ctx, BatchWork& w, int batch, int M, const l
   L.batch = batch;
   L.M = M;
   L.fp32 = fp32;
+  L.plain = (flags & LHAF_PLAIN_ACCUM) ? 1 : 0;
   L.B_stride = per_item_B ? (long long)M * M : 0;
   cudaStream_t s = ctx->stream;
 
@@ -109,71 +145,72 @@ lhaf_status prepare_batch(lhaf_ctx* ctx, BatchWork& w, int batch, int M, const l
     }
     item_h[i] = st[i] != LHAF_OK ? INT_MAX : (plans[i].N == 0 ? -1 : plans[i].h);
   }
-  // ---- sieves: one per item, or its zero-digit groups (numbered in order) ----
+
+  // ---- sieves, sorted into classes (series mode, working dimension), items in order ----
+  const char* env_stage = std::getenv("LHAF_STAGE");
+  const bool stage_ok = !(env_stage && env_stage[0] == '0');
   struct Job {
     int item;
     Plan pl;
-    uint64_t base;  // first term number of the job in its item's numbering
   };
   std::vector<Job> jobs;
-  std::vector<int> job_begin(batch + 1, 0);
   for (int i = 0; i < batch; i++) {
-    job_begin[i] = (int)jobs.size();
     if (!(st[i] == LHAF_OK && plans[i].N > 0)) continue;
     std::vector<Plan> subs;
     if (!(flags & LHAF_NO_ZERO_SPLIT) && split_zero_digits(plans[i], subs)) {
-      uint64_t base = 0;
-      for (Plan& sp : subs) {
-        const uint64_t T = sp.T;
-        jobs.push_back({i, std::move(sp), base});
-        base += T;
-      }
+      for (Plan& sp : subs) jobs.push_back({i, std::move(sp)});
     } else {
-      jobs.push_back({i, plans[i], 0});
+      jobs.push_back({i, plans[i]});
     }
   }
-  job_begin[batch] = (int)jobs.size();
   const int n_jobs = (int)jobs.size();
+  std::vector<std::vector<int>> members(2 * kNumBounds);
+  for (int j = 0; j < n_jobs; j++) {
+    const Plan& pl = jobs[j].pl;
+    int b = 0;
+    while (b + 1 < kNumBounds && pl.nd > kClassBounds[b]) b++;
+    const bool staged = stage_ok && pl.h <= kStageMaxDegree;
+    members[(staged ? 0 : kNumBounds) + b].push_back(j);
+  }
 
-  // ---- per-sieve descriptors, slot-matrix pool, costs ----
+  // ---- descriptors and slot-matrix pool, class after class ----
   const int n_desc = std::max(n_jobs, 1);
   if (!w.h_items.reserve(sizeof(BatchItem) * n_desc) || !w.items.reserve(sizeof(BatchItem) * n_desc) ||
       !w.h_item_h.reserve(sizeof(int) * batch) || !w.item_h.reserve(sizeof(int) * batch) ||
-      !w.h_unit_begin.reserve(sizeof(int) * (batch + 1)) || !w.unit_begin.reserve(sizeof(int) * (batch + 1)) ||
-      !w.out.reserve(sizeof(double2) * batch) || !w.h_out.reserve(sizeof(double2) * batch))
+      !w.acc.reserve(sizeof(double) * 4 * batch) || !w.out.reserve(sizeof(double2) * batch) ||
+      !w.h_out.reserve(sizeof(double2) * batch))
     return LHAF_ENOMEM;
-  BatchItem* hitems = static_cast<BatchItem*>(w.h_items.p);
-  std::memset(hitems, 0, sizeof(BatchItem) * n_desc);
+  BatchItem* desc = static_cast<BatchItem*>(w.h_items.p);
+  std::memset(desc, 0, sizeof(BatchItem) * n_desc);
+  std::vector<int> order;  // descriptor index -> job
   long long pool = 0;
-  int nd_max = 0, H_max = 0, Hl_max = 0, rep = -1;
-  double cost_max = -1.0, cost_total = 0.0;
-  std::vector<double> fpt(n_desc, 0.0);
-  for (int j = 0; j < n_jobs; j++) {
-    const Plan& pl = jobs[j].pl;
-    fill_params(pl, fp32, false, 32, flags, hitems[j].p);
-    hitems[j].chat_off = pool;
-    hitems[j].src = jobs[j].item;
-    for (int q = 0; q < kMaxDim; q++) hitems[j].slot_mode[q] = q < 2 * pl.P ? pl.slot_mode[q] : -1;
-    pool += (long long)pl.nd * pl.nd;
-    nd_max = std::max(nd_max, pl.nd);
-    H_max = std::max(H_max, pl.H);
-    Hl_max = std::max(Hl_max, pl.Hl);
-    fpt[j] = lhaf_model_flops_per_term(pl.nd, pl.h, pl.bord);
-    const double c = fpt[j] * (double)pl.T;
-    cost_total += c;
-    if (c > cost_max) {
-      cost_max = c;
-      rep = j;
+  for (int c = 0; c < 2 * kNumBounds; c++) {
+    if (members[c].empty()) continue;
+    GClass cl;
+    cl.staged = c < kNumBounds;
+    cl.desc_off = (long long)order.size();
+    cl.n_jobs = (int)members[c].size();
+    for (int j : members[c]) {
+      const Plan& pl = jobs[j].pl;
+      BatchItem& d = desc[order.size()];
+      fill_params(pl, fp32, cl.staged, 32, flags, d.p);
+      d.p.t_end = pl.T;  // the sieve's term count (the kernel sets the per-chunk range)
+      d.chat_off = pool;
+      d.base = 0;
+      d.src = jobs[j].item;
+      for (int q = 0; q < kMaxDim; q++) d.slot_mode[q] = q < 2 * pl.P ? pl.slot_mode[q] : -1;
+      pool += (long long)pl.nd * pl.nd;
+      order.push_back(j);
     }
+    L.classes.push_back(std::move(cl));
   }
   std::memcpy(w.h_item_h.p, item_h.data(), sizeof(int) * batch);
   if (!w.chat.reserve(sizeof(double2) * std::max<long long>(pool, 1)) ||
       (fp32 && !w.chat32.reserve(sizeof(float2) * std::max<long long>(pool, 1))))
     return LHAF_ENOMEM;
   L.n_desc = n_jobs;
-  // descriptors first (the device gather reads them)
   if (n_jobs > 0 &&
-      cudaMemcpyAsync(w.items.p, hitems, sizeof(BatchItem) * n_jobs, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      cudaMemcpyAsync(w.items.p, desc, sizeof(BatchItem) * n_jobs, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return (lhaf_status)record_cuda(cudaPeekAtLastError(), "batched descriptors");
   L.h2d += sizeof(BatchItem) * (uint64_t)n_jobs;
   if (dev_inputs) {
@@ -181,190 +218,203 @@ lhaf_status prepare_batch(lhaf_ctx* ctx, BatchWork& w, int batch, int M, const l
                             n_jobs, (double2*)w.chat.p, fp32 ? (float2*)w.chat32.p : nullptr, s) != cudaSuccess)
       return (lhaf_status)record_cuda(cudaPeekAtLastError(), "batch gather");
     if (n_jobs > 0) L.prep_launches++;
-  } else {
-    L.h2d += (uint64_t)pool * (fp32 ? sizeof(float2) : sizeof(double2));
-    if (!w.h_chat.reserve(sizeof(double2) * std::max<long long>(pool, 1))) return LHAF_ENOMEM;
+  } else if (pool > 0) {
+    if (!w.h_chat.reserve(sizeof(double2) * pool)) return LHAF_ENOMEM;
     std::complex<double>* hc = static_cast<std::complex<double>*>(w.h_chat.p);
-    for (int j = 0; j < n_jobs; j++) {
-      const int i = jobs[j].item;
-      build_chat_host(jobs[j].pl, M, B + (size_t)i * L.B_stride, gamma ? gamma + (size_t)i * M : nullptr,
-                      hc + hitems[j].chat_off);
+    for (int d = 0; d < n_jobs; d++) {
+      const int i = jobs[order[d]].item;
+      build_chat_host(jobs[order[d]].pl, M, B + (size_t)i * L.B_stride, gamma ? gamma + (size_t)i * M : nullptr,
+                      hc + desc[d].chat_off);
     }
     if (fp32) {
-      if (!w.h_chat32.reserve(sizeof(float2) * std::max<long long>(pool, 1))) return LHAF_ENOMEM;
+      if (!w.h_chat32.reserve(sizeof(float2) * pool)) return LHAF_ENOMEM;
       float2* h32 = static_cast<float2*>(w.h_chat32.p);
       for (long long e = 0; e < pool; e++) h32[e] = make_float2((float)hc[e].real(), (float)hc[e].imag());
       if (cudaMemcpyAsync(w.chat32.p, h32, sizeof(float2) * pool, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return (lhaf_status)record_cuda(cudaPeekAtLastError(), "batched slot matrices");
-    } else if (pool > 0) {
-      if (cudaMemcpyAsync(w.chat.p, hc, sizeof(double2) * pool, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return (lhaf_status)record_cuda(cudaPeekAtLastError(), "batched slot matrices");
+    } else if (cudaMemcpyAsync(w.chat.p, hc, sizeof(double2) * pool, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      return (lhaf_status)record_cuda(cudaPeekAtLastError(), "batched slot matrices");
     }
+    L.h2d += (uint64_t)pool * cs;
   }
 
-  // Items of degree <= kStageMaxDegree stage their term polynomials and finish them one term per
-  // thread inside the CTA; larger degrees finish each term in the team (inline).
-  const char* env_stage = std::getenv("LHAF_STAGE");
-  const bool stage_ok = !(env_stage && env_stage[0] == '0');
-  bool any_inline = false;
-  int h_max_staged = 0;
-  for (const Job& jb : jobs) {
-    if (stage_ok && jb.pl.h <= kStageMaxDegree) {
-      h_max_staged = std::max(h_max_staged, jb.pl.h);
-    } else {
-      any_inline = true;
-    }
-  }
-
-  // ---- team size: tuned on the costliest item, shared-memory layout for the largest ----
-  int team = 16, occ = 0;
-  const void* chat_pool = fp32 ? w.chat32.p : w.chat.p;
-  size_t team_bytes = 0, items_bytes = 0;
-  if (rep >= 0) {
-    const char* chatp = static_cast<const char*>(chat_pool) + (size_t)hitems[rep].chat_off * (fp32 ? 8 : 16);
-    int occ_rep = 0;
-    // tuned with the single-lhaf kernel on the costliest item's slot matrix (in the pool)
-    team = pick_team(ctx, fp32, jobs[rep].pl, false, 1, chatp, &occ_rep);
-    if (team == 0) team = 32;
-    auto layout = [&](int g) {
-      team_bytes = team_shared_bytes(fp32, nd_max, H_max, 0, !any_inline);
-      items_bytes = cta_table_bytes(fp32, Hl_max, H_max);
-      // the fused series reuses the team area: (4h + 5) entries per CTA thread
-      const size_t series_bytes = (size_t)(4 * h_max_staged + 5) * cta_threads(g) * (fp32 ? 8 : 16);
-      if (h_max_staged > 0 && (size_t)teams_per_cta(g) * team_bytes < series_bytes)
-        team_bytes = ((series_bytes + teams_per_cta(g) - 1) / teams_per_cta(g) + 15) & ~(size_t)15;
-    };
-    layout(team);
-    while (items_bytes + (size_t)teams_per_cta(team) * team_bytes > 227 * 1024 && team < 128) {
-      team *= 2;
-      layout(team);
-    }
-    occ = batched_ctas_per_sm(fp32, team, items_bytes + (size_t)teams_per_cta(team) * team_bytes);
-    if (occ <= 0) return LHAF_ETOOBIG;
-    occ = ctas_per_sm_override(occ);
-  }
-  const int TEAMS = teams_per_cta(team);
-
-  // ---- work units: term ranges of similar cost, queue ordered longest first ----
-  std::vector<BatchUnit> units;
-  std::vector<double> ucost;
-  std::vector<int> unit_begin(batch + 1, 0);
-  const long long n_ctas = (long long)ctx->sms * std::max(occ, 1);
-  const double target = cost_total / (double)(n_ctas * 8);
-  uint64_t terms_run = 0;
-  double flops_run = 0.0;
-  for (int i = 0; i < batch; i++) {
-    unit_begin[i] = (int)units.size();
-    for (int j = job_begin[i]; j < job_begin[i + 1]; j++) {
-      // this job's part of the item's term range [range_tb, range_te) (whole range for batches)
-      const uint64_t base = jobs[j].base, T = jobs[j].pl.T;
-      const uint64_t lo = range_tb > base ? std::min<uint64_t>(range_tb - base, T) : 0;
-      const uint64_t hi = range_te > base ? std::min<uint64_t>(range_te - base, T) : 0;
-      if (hi <= lo) continue;
-      terms_run += hi - lo;
-      flops_run += fpt[j] * (double)(hi - lo);
-      uint64_t ut = (uint64_t)std::ceil(target / std::max(fpt[j], 1.0));
-      ut = std::min<uint64_t>(ut, 4096);  // bounds the per-CTA staging region
-      ut = std::max<uint64_t>(ut, (uint64_t)TEAMS);
-      ut = ((ut + TEAMS - 1) / TEAMS) * TEAMS;
-      for (uint64_t t0 = lo; t0 < hi; t0 += ut) {
-        BatchUnit u;
-        u.item = j;
-        u.pad = 0;
-        u.t0 = t0;
-        u.t1 = std::min<uint64_t>(hi, t0 + ut);
-        u.stage_off = -1;
-        u.w_off = 0;
-        units.push_back(u);
-        ucost.push_back(fpt[j] * (double)(u.t1 - u.t0));
+  // ---- per class: team size, layout, occupancy, chunks, launches and segments ----
+  std::vector<long long> chunk_off_all, seg_begin_all;
+  std::vector<int> seg_item_all;
+  size_t stage_bytes_max = 0, wstage_max = 0, entries_max = 0;
+  const void* pool_ptr = fp32 ? w.chat32.p : w.chat.p;
+  for (GClass& cl : L.classes) {
+    int nd_max = 0, P_max = 0, Hl_max = 0, H_max = 0;
+    long long rep = cl.desc_off;
+    double cost_max = -1.0;
+    for (long long d = cl.desc_off; d < cl.desc_off + cl.n_jobs; d++) {
+      const Plan& pl = jobs[order[d]].pl;
+      nd_max = std::max(nd_max, pl.nd);
+      P_max = std::max(P_max, pl.P);
+      Hl_max = std::max(Hl_max, pl.Hl);
+      H_max = std::max(H_max, pl.H);
+      cl.h_max = std::max(cl.h_max, pl.h);
+      cl.rows_max = std::max(cl.rows_max, pl.bord ? 2 * pl.h + 1 : pl.h);
+      const double fpt = lhaf_model_flops_per_term(pl.nd, pl.h, pl.bord);
+      L.terms += pl.T;
+      L.flops += fpt * (double)pl.T;
+      L.h_max = std::max(L.h_max, pl.h);
+      L.nd_max = std::max(L.nd_max, pl.nd);
+      if (fpt * (double)pl.T > cost_max) {
+        cost_max = fpt * (double)pl.T;
+        rep = d;
       }
     }
+    // team tuned on the class's costliest sieve (its slot matrix is in the pool already); a
+    // staged trial stages into the context's buffer, grown here for it when that is possible
+    const Plan& rp = jobs[order[rep]].pl;
+    if (cl.staged) {
+      const int rows = rp.bord ? 2 * rp.h + 1 : rp.h;
+      const uint64_t trial = std::min<uint64_t>(rp.T, (uint64_t)ctx->partial_cap);
+      ensure_stage(ctx, (size_t)rows * cs * trial, trial);  // on failure the tuner skips staged trials
+    }
+    int occ = 0;
+    const char* chatp = static_cast<const char*>(pool_ptr) + (size_t)desc[rep].chat_off * cs;
+    int team = pick_team(ctx, fp32, rp, cl.staged, 3, chatp, &occ);
+    if (team == 0) team = 32;
+    auto layout = [&](int g) {
+      cl.team_bytes = (int)team_shared_bytes(fp32, nd_max, H_max, P_max, cl.staged);
+      cl.items_bytes = (int)cta_table_bytes(fp32, Hl_max, H_max);
+      return (size_t)cl.items_bytes + (size_t)teams_per_cta(g) * (size_t)cl.team_bytes;
+    };
+    while (layout(team) > 227 * 1024 && team < 128) team *= 2;
+    const size_t smem = layout(team);
+    if (smem > 227 * 1024) return LHAF_ETOOBIG;
+    const int occ_g = grouped_ctas_per_sm(fp32, team, smem, cl.staged);
+    if (occ_g <= 0) return LHAF_ETOOBIG;
+    occ = ctas_per_sm_override(std::min(occ > 0 ? occ : occ_g, occ_g));
+    cl.team = team;
+    cl.tpc = teams_per_cta(team);
+    L.team = std::max(L.team, team);
+    // chunks of tpc terms per sieve; this class's offsets follow the previous classes'
+    cl.chunk_off = (long long)chunk_off_all.size();
+    std::vector<long long> coff(cl.n_jobs + 1, 0);
+    for (int q = 0; q < cl.n_jobs; q++) {
+      const uint64_t T = jobs[order[cl.desc_off + q]].pl.T;
+      coff[q + 1] = coff[q] + (long long)((T + cl.tpc - 1) / cl.tpc);
+    }
+    chunk_off_all.insert(chunk_off_all.end(), coff.begin(), coff.end());
+    // columns per launch: staged rows and weights plus the value entries, within the budget
+    const size_t col_bytes =
+        (cl.staged ? (size_t)cl.rows_max * cs + sizeof(double) : (size_t)0) + 4 * sizeof(double);
+    long long cols = (long long)(kLaunchBytes / col_bytes);
+    cols = std::max<long long>(cols / cl.tpc, 1) * cl.tpc;
+    cl.cols_cap = cols;
+    const long long chunks_per_launch = cols / cl.tpc;
+    const long long n_chunks = coff[cl.n_jobs];
+    const uint64_t max_ctas = (uint64_t)ctx->sms * (uint64_t)occ;
+    for (long long c0 = 0; c0 < n_chunks; c0 += chunks_per_launch) {
+      GLaunch lg;
+      lg.c0 = c0;
+      lg.c1 = std::min(n_chunks, c0 + chunks_per_launch);
+      unsigned long long rounds = 1;
+      lg.grid = (int)balanced_grid((uint64_t)(lg.c1 - lg.c0), 1, max_ctas, &rounds);
+      lg.rounds = (int)rounds;
+      // item segments over the launch's columns: adjacent ranges, consecutive sieves of one item
+      // merged; boundaries b_0 = 0 < b_1 < ... < b_n_seg = columns
+      lg.sb_off = (long long)seg_begin_all.size();
+      lg.si_off = (long long)seg_item_all.size();
+      seg_begin_all.push_back(0);
+      int cur = -1;
+      for (int q = 0; q < cl.n_jobs; q++) {
+        const long long a = std::max(coff[q], lg.c0), b = std::min(coff[q + 1], lg.c1);
+        if (b <= a) continue;
+        const int item = jobs[order[cl.desc_off + q]].item;
+        const long long eb = (b - lg.c0) * cl.tpc;
+        if (item == cur) {
+          seg_begin_all.back() = eb;
+        } else {
+          seg_begin_all.push_back(eb);
+          seg_item_all.push_back(item);
+          lg.n_seg++;
+          cur = item;
+        }
+      }
+      cl.launches.push_back(lg);
+      if (cl.staged) {
+        stage_bytes_max = std::max(stage_bytes_max, (size_t)cl.rows_max * cs * (size_t)cols);
+        wstage_max = std::max(wstage_max, (size_t)cols);
+      }
+      entries_max = std::max(entries_max, (size_t)((lg.c1 - lg.c0) * cl.tpc));
+    }
   }
-  unit_begin[batch] = (int)units.size();
-  const int n_units = (int)units.size();
-  std::vector<int> queue(n_units);
-  std::iota(queue.begin(), queue.end(), 0);
-  std::stable_sort(queue.begin(), queue.end(), [&](int a, int b) { return ucost[a] > ucost[b]; });
-
-  // Staged units: each CTA stages the polynomials of the unit it runs in a private region of
-  // region_elems entries (the largest staged unit) and finishes them itself.
-  const size_t cs_b = fp32 ? sizeof(float2) : sizeof(double2);
-  const long long grid_b = std::min<long long>(n_ctas, std::max(n_units, 1));
-  long long region_elems = 0, w_region = 0;
-  for (const BatchUnit& u : units) {
-    const Plan& pl = jobs[u.item].pl;
-    if (!(stage_ok && pl.h <= kStageMaxDegree)) continue;
-    const long long rows = pl.bord ? 2 * (long long)pl.h + 1 : (long long)pl.h;
-    region_elems = std::max(region_elems, rows * (long long)(u.t1 - u.t0));
-    w_region = std::max(w_region, (long long)(u.t1 - u.t0));
-  }
-  for (BatchUnit& u : units) {
-    const Plan& pl = jobs[u.item].pl;
-    const bool staged_u = stage_ok && pl.h <= kStageMaxDegree;
-    u.stage_off = staged_u ? region_elems : -1;
-    u.w_off = staged_u ? w_region : 0;
-  }
-  if (region_elems > 0 && (!w.stage.reserve((size_t)region_elems * grid_b * cs_b) ||
-                           !w.wstage.reserve((size_t)w_region * grid_b * sizeof(double))))
+  if (!w.h_chunks.reserve(sizeof(long long) * std::max<size_t>(chunk_off_all.size(), 1)) ||
+      !w.chunks.reserve(sizeof(long long) * std::max<size_t>(chunk_off_all.size(), 1)) ||
+      !w.h_seg_begin.reserve(sizeof(long long) * std::max<size_t>(seg_begin_all.size(), 1)) ||
+      !w.seg_begin.reserve(sizeof(long long) * std::max<size_t>(seg_begin_all.size(), 1)) ||
+      !w.h_seg_item.reserve(sizeof(int) * std::max<size_t>(seg_item_all.size(), 1)) ||
+      !w.seg_item.reserve(sizeof(int) * std::max<size_t>(seg_item_all.size(), 1)) ||
+      !w.entries.reserve(4 * sizeof(double) * std::max<size_t>(entries_max, 1)) ||
+      (stage_bytes_max > 0 && (!w.stage.reserve(stage_bytes_max) || !w.wstage.reserve(sizeof(double) * wstage_max))))
     return LHAF_ENOMEM;
-
-  if (!w.h_units.reserve(sizeof(BatchUnit) * std::max(n_units, 1)) ||
-      !w.units.reserve(sizeof(BatchUnit) * std::max(n_units, 1)) ||
-      !w.h_queue.reserve(sizeof(int) * std::max(n_units, 1)) || !w.queue.reserve(sizeof(int) * std::max(n_units, 1)) ||
-      !w.next.reserve(sizeof(int)) || !w.partials.reserve(sizeof(double) * 4 * (size_t)std::max(n_units, 1) * TEAMS))
-    return LHAF_ENOMEM;
-  std::memcpy(w.h_units.p, units.data(), sizeof(BatchUnit) * n_units);
-  std::memcpy(w.h_queue.p, queue.data(), sizeof(int) * n_units);
-  std::memcpy(w.h_unit_begin.p, unit_begin.data(), sizeof(int) * (batch + 1));
+  std::memcpy(w.h_chunks.p, chunk_off_all.data(), sizeof(long long) * chunk_off_all.size());
+  std::memcpy(w.h_seg_begin.p, seg_begin_all.data(), sizeof(long long) * seg_begin_all.size());
+  std::memcpy(w.h_seg_item.p, seg_item_all.data(), sizeof(int) * seg_item_all.size());
   const bool ok =
-      (n_units == 0 ||
-       (cudaMemcpyAsync(w.units.p, w.h_units.p, sizeof(BatchUnit) * n_units, cudaMemcpyHostToDevice, s) ==
-            cudaSuccess &&
-        cudaMemcpyAsync(w.queue.p, w.h_queue.p, sizeof(int) * n_units, cudaMemcpyHostToDevice, s) == cudaSuccess)) &&
-      cudaMemcpyAsync(w.unit_begin.p, w.h_unit_begin.p, sizeof(int) * (batch + 1), cudaMemcpyHostToDevice, s) ==
-          cudaSuccess &&
+      (chunk_off_all.empty() || cudaMemcpyAsync(w.chunks.p, w.h_chunks.p, sizeof(long long) * chunk_off_all.size(),
+                                                cudaMemcpyHostToDevice, s) == cudaSuccess) &&
+      (seg_begin_all.empty() || cudaMemcpyAsync(w.seg_begin.p, w.h_seg_begin.p,
+                                                sizeof(long long) * seg_begin_all.size(), cudaMemcpyHostToDevice,
+                                                s) == cudaSuccess) &&
+      (seg_item_all.empty() || cudaMemcpyAsync(w.seg_item.p, w.h_seg_item.p, sizeof(int) * seg_item_all.size(),
+                                               cudaMemcpyHostToDevice, s) == cudaSuccess) &&
       cudaMemcpyAsync(w.item_h.p, w.h_item_h.p, sizeof(int) * batch, cudaMemcpyHostToDevice, s) == cudaSuccess;
-  if (!ok) return (lhaf_status)record_cuda(cudaPeekAtLastError(), "batched work units");
-  L.h2d += (sizeof(BatchUnit) + sizeof(int)) * (uint64_t)n_units + sizeof(int) * (uint64_t)(2 * batch + 1);
+  if (!ok) return (lhaf_status)record_cuda(cudaPeekAtLastError(), "batched launch tables");
+  L.h2d += sizeof(long long) * (chunk_off_all.size() + seg_begin_all.size()) + sizeof(int) * seg_item_all.size() +
+           sizeof(int) * (size_t)batch;
   if (cudaEventRecord(w.uploaded, s) != cudaSuccess)
     return (lhaf_status)record_cuda(cudaPeekAtLastError(), "cudaEventRecord");
-
-  L.team = team;
-  L.teams = TEAMS;
-  L.team_bytes = (int)team_bytes;
-  L.items_bytes = (int)items_bytes;
-  L.grid = (int)grid_b;
-  L.n_units = n_units;
-  L.region_elems = region_elems;
-  L.terms = terms_run;
-  L.flops = flops_run;
-  for (const Job& jb : jobs) L.h_max = std::max(L.h_max, jb.pl.h);
-  L.nd_max = nd_max;
   return LHAF_OK;
 }
 
-// The launches of a prepared batch on stream s: queue reset, persistent kernel, per-item
-// reduction into out (device, batch complex values).
-lhaf_status enqueue_batch(BatchWork& w, const BatchLaunch& L, double2* out, cudaStream_t s,
-                          double* out_dd = nullptr) {
-  if (cudaMemsetAsync(w.next.p, 0, sizeof(int), s) != cudaSuccess)
-    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "batched queue reset");
-  if (L.n_units > 0) {
-    const void* chat_pool = L.fp32 ? w.chat32.p : w.chat.p;
-    if (launch_batched(L.fp32, L.team, chat_pool, (const BatchItem*)w.items.p, (const BatchUnit*)w.units.p,
-                       (const int*)w.queue.p, L.n_units, (int*)w.next.p, (double*)w.partials.p, L.team_bytes,
-                       L.items_bytes, L.grid, s, L.region_elems ? w.stage.p : nullptr,
-                       L.region_elems ? (double*)w.wstage.p : nullptr) != cudaSuccess)
-      return (lhaf_status)record_cuda(cudaPeekAtLastError(), "batched kernel");
+// The launches of a prepared batch on stream s: accumulator reset; per class and chunk range the
+// grouped terms kernel, the series (staged classes) and the segmented reduction; then the per-item
+// scaling into out (device, batch complex values).
+lhaf_status enqueue_batch(BatchWork& w, const BatchLaunch& L, double2* out, cudaStream_t s) {
+  if (cudaMemsetAsync(w.acc.p, 0, sizeof(double) * 4 * L.batch, s) != cudaSuccess)
+    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "batched accumulator reset");
+  const void* pool_ptr = L.fp32 ? w.chat32.p : w.chat.p;
+  const BatchItem* items = (const BatchItem*)w.items.p;
+  const long long* chunks = (const long long*)w.chunks.p;
+  const long long* segb = (const long long*)w.seg_begin.p;
+  const int* segi = (const int*)w.seg_item.p;
+  for (const GClass& cl : L.classes) {
+    const BatchItem* cj = items + cl.desc_off;
+    const long long* cc = chunks + cl.chunk_off;
+    for (const GLaunch& lg : cl.launches) {
+      cudaError_t e = launch_grouped_terms(
+          L.fp32, cl.team, pool_ptr, cj, cl.n_jobs, cc, lg.c0, lg.c1, lg.grid, lg.rounds, 0ull, ~0ull,
+          cl.team_bytes, cl.items_bytes, cl.staged ? nullptr : (double*)w.entries.p,
+          cl.staged ? w.stage.p : nullptr, cl.staged ? (double*)w.wstage.p : nullptr,
+          cl.staged ? cl.cols_cap : 0, s, cl.staged ? 0 : 1);
+      if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "grouped terms kernel");
+      if (cl.staged) {
+        e = launch_series_values(L.fp32, w.stage.p, (const double*)w.wstage.p, (lg.c1 - lg.c0) * cl.tpc, cl.cols_cap,
+                                 cj, cl.n_jobs, cc, lg.c0, cl.tpc, cl.h_max, (double*)w.entries.p, s);
+        if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "series kernel");
+      }
+      e = launch_segment_reduce((const double*)w.entries.p, segb + lg.sb_off, segi + lg.si_off, lg.n_seg, L.plain,
+                                (double*)w.acc.p, s);
+      if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "segmented reduction");
+    }
   }
-  if (launch_batch_reduce((const double*)w.partials.p, (const int*)w.unit_begin.p, (const int*)w.item_h.p, L.teams,
-                          L.batch, out, s, out_dd) != cudaSuccess)
-    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "batched reduction");
+  if (launch_item_finalize((const double*)w.acc.p, (const int*)w.item_h.p, L.batch, out, s) != cudaSuccess)
+    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "batched scaling");
   return LHAF_OK;
 }
 
-// Kernels of one enqueue_batch: the persistent kernel (when there is work) and the reduction.
-int enqueue_launches(const BatchLaunch& L) { return (L.n_units > 0 ? 1 : 0) + 1; }
+// Kernels of one enqueue_batch.
+int enqueue_launches(const BatchLaunch& L) {
+  int n = 1;
+  for (const GClass& cl : L.classes)
+    for (const GLaunch& lg : cl.launches) n += (cl.staged ? 2 : 1) + (lg.n_seg > 0 ? 1 : 0);
+  return n;
+}
 
 void fill_stats(const BatchLaunch& L, lhaf_stats* stats) {
   stats->h2d_bytes = L.h2d;
@@ -372,7 +422,7 @@ void fill_stats(const BatchLaunch& L, lhaf_stats* stats) {
   stats->terms = L.terms;
   stats->n_dim = L.nd_max;
   stats->h = L.h_max;
-  stats->pairs = L.n_units;
+  stats->pairs = (int32_t)L.classes.size();
   stats->team = L.team;
   stats->flops_model = L.flops;
 }
@@ -418,31 +468,6 @@ extern "C" lhaf_status lhaf_batched(lhaf_ctx* ctx, int batch, int M, const lhaf_
   if (!dev) std::memcpy(out, w.h_out.p, sizeof(double2) * batch);
   return LHAF_OK;
 }
-
-namespace lhafgpu {
-
-lhaf_status run_split_single(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128* gamma, const int32_t* reps,
-                             uint32_t flags, bool dev_inputs, uint64_t tb, uint64_t te, double* dd_dst,
-                             double2* val_dst, lhaf_stats* stats) {
-  std::vector<lhaf_status> st;
-  BatchLaunch L;
-  BatchWork& w = ctx->bw;
-  lhaf_status rc = prepare_batch(ctx, w, 1, M, B, gamma, reps, flags & ~LHAF_BATCH_B_PER_ITEM, dev_inputs, st, L, tb,
-                                 te);
-  if (rc != LHAF_OK) return rc;
-  if (st[0] != LHAF_OK) return st[0];
-  if (stats) cudaEventRecord(ctx->ev0, ctx->stream);
-  rc = enqueue_batch(w, L, val_dst, ctx->stream, dd_dst);
-  if (rc != LHAF_OK) return rc;
-  if (stats) {
-    cudaEventRecord(ctx->ev1, ctx->stream);
-    fill_stats(L, stats);
-    stats->kernel_ms = 0.0;
-  }
-  return LHAF_OK;
-}
-
-}  // namespace lhafgpu
 
 // ---------------------------------------------------------------------------------------------
 // Batched plan: planning, tuning and buffers once; the launches captured in a CUDA graph.
@@ -532,7 +557,7 @@ extern "C" lhaf_status lhaf_batched_plan_create(lhaf_ctx* ctx, int batch, int M,
   if (rc != LHAF_OK) return fail(rc);
   if (const cudaError_t e_ = cudaStreamSynchronize(ctx->stream); e_ != cudaSuccess)
     return fail((lhaf_status)record_cuda(e_, "cudaStreamSynchronize"));
-  // capture: gather -> queue reset -> persistent kernel -> reduction
+  // capture: gather -> accumulator reset -> grouped launches -> scaling
   if (cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking) != cudaSuccess)
     return fail((lhaf_status)record_cuda(cudaPeekAtLastError(), "capture stream"));
   if (cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
@@ -594,10 +619,10 @@ extern "C" lhaf_status lhaf_batched_plan_exec(lhaf_batch_plan* pl, const lhaf_c1
     for (int i = 0; i < batch; i++) item_status[i] = st[i];
   if (stats) {
     fill_stats(pl->L, stats);
-    // a replay copies only the inputs and results; its graph holds the gather and enqueue_batch
+    // a replay copies only the inputs and results; its graph holds the gather and the launches
     stats->h2d_bytes = dev ? 0 : sizeof(lhaf_c128) * (uint64_t)(pl->B_elems + (pl->with_gamma ? pl->g_elems : 0));
     stats->d2h_bytes = dev ? 0 : ob;
-    stats->launches = 1 + enqueue_launches(pl->L);
+    stats->launches = (pl->L.n_desc > 0 ? 1 : 0) + enqueue_launches(pl->L);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     stats->kernel_ms = ms;

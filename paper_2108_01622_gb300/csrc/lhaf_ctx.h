@@ -59,19 +59,24 @@ struct HostBuf {
   }
 };
 
-// Buffers of one batched evaluation: the context's own (lhaf_batched) or a batched plan's, whose
-// captured graph holds these addresses.
+// Buffers of one grouped evaluation: the sieves (items, or their zero-digit groups) of one loop
+// hafnian (ctx->gw) or of a batch (ctx->bw, or a batched plan's own, whose captured graph holds
+// these addresses).
 struct BatchWork {
-  DevBuf items, units, queue, next, partials, unit_begin, item_h, chat, chat32, out, stage, wstage, in_B, in_gamma;
-  HostBuf h_items, h_units, h_queue, h_unit_begin, h_item_h, h_chat, h_chat32, h_out, h_in;
+  DevBuf items;      // sieve descriptors (BatchItem)
+  DevBuf chunks;     // chunk offsets per sieve (long long), class after class
+  DevBuf seg_begin;  // per launch: entry offsets of its item segments (long long)
+  DevBuf seg_item;   // per launch: the item of each segment (int)
+  DevBuf item_h, acc, entries, chat, chat32, out, stage, wstage, in_B, in_gamma;
+  HostBuf h_items, h_chunks, h_seg_begin, h_seg_item, h_item_h, h_chat, h_chat32, h_out, h_in;
   cudaEvent_t uploaded = nullptr;  // after the last copies that read the pinned buffers above
   void release() {
     if (uploaded) cudaEventDestroy(uploaded);
     uploaded = nullptr;
-    for (DevBuf* b : {&items, &units, &queue, &next, &partials, &unit_begin, &item_h, &chat, &chat32, &out, &stage,
+    for (DevBuf* b : {&items, &chunks, &seg_begin, &seg_item, &item_h, &acc, &entries, &chat, &chat32, &out, &stage,
                       &wstage, &in_B, &in_gamma})
       b->release();
-    for (HostBuf* b : {&h_items, &h_units, &h_queue, &h_unit_begin, &h_item_h, &h_chat, &h_chat32, &h_out, &h_in})
+    for (HostBuf* b : {&h_items, &h_chunks, &h_seg_begin, &h_seg_item, &h_item_h, &h_chat, &h_chat32, &h_out, &h_in})
       b->release();
   }
 };
@@ -101,6 +106,7 @@ struct lhaf_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, tev0 = nullptr, tev1 = nullptr;
   // batched form and adjoint
   BatchWork bw;
+  BatchWork gw;  // one loop hafnian's zero-digit groups (descriptors in items, chunk offsets in units)
   DevBuf b_gpart, b_gout;
   HostBuf hb_gout;
   // measured best team size per problem shape
@@ -116,12 +122,9 @@ int pick_team(lhaf_ctx* ctx, bool fp32, const Plan& pl, bool staged, int family,
 // Fill the sieve description of a plan (everything but the term range and the grid).
 void fill_params(const Plan& pl, bool fp32, bool staged, int team, uint32_t flags, TermParams& p);
 int ctas_per_sm_override(int occ);
-// One loop hafnian through the persistent batched kernel over its zero-digit groups, restricted
-// to [tb, te) of the group numbering: the unscaled double-double partial to dd_dst and/or the
-// scaled value to val_dst (device pointers, either may be NULL), ordered on ctx->stream. The caller
-// holds ctx->mu and has validated host inputs.
-lhaf_status run_split_single(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128* gamma, const int32_t* reps,
-                             uint32_t flags, bool dev_inputs, uint64_t tb, uint64_t te, double* dd_dst,
-                             double2* val_dst, lhaf_stats* stats);
+// Grow the context's staging buffer (synchronising its stream first) to at least `bytes` of
+// coefficient rows and `terms` weights; false (and no buffer) if the allocation fails.
+bool ensure_stage(lhaf_ctx* ctx, size_t bytes, size_t terms);
+
 uint64_t balanced_grid(uint64_t n, int tpc, uint64_t max_ctas, unsigned long long* rounds);
 }  // namespace lhafgpu

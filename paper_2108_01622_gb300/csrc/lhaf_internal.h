@@ -32,22 +32,19 @@ struct TermParams {
   unsigned long long t_begin, t_end;  // evaluated-term index range
   unsigned long long rounds;          // terms per team (uniform, last round may be idle)
   unsigned long long total_teams;
+  unsigned long long t_lo;            // terms below t_lo are outside the range (weight 0)
+  int stage_pad;                      // 1: stage out-of-range terms too, with weight 0
+  int pad_;
 };
 
-// Batched form: one item (loop hafnian) and one work unit (a term range of one item).
+// One sieve of a grouped launch: a loop hafnian's whole sieve or one of its zero-digit groups.
 struct BatchItem {
-  TermParams p;         // the item's sieve (t_begin/t_end/rounds/total_teams set per unit)
+  TermParams p;         // the sieve (t_end = its term count; the kernel sets the chunk range)
   long long chat_off;   // element offset of the item's slot matrix in the pool
+  unsigned long long base;  // first term number of this sieve in its loop hafnian's numbering
   int src;              // index of the loop hafnian (its B and gamma) this sieve belongs to
   int pad;
   int slot_mode[kMaxDim];
-};
-struct BatchUnit {
-  int item;
-  int pad;
-  unsigned long long t0, t1;
-  long long stage_off;  // staged unit: entries of the per-CTA staging region; -1: inline unit
-  long long w_off;      // staged unit: entries of the per-CTA weight region
 };
 
 // Launch the FP64 (fp32 = false) or FP32 term kernel. chat is the bordered slot matrix (nd x nd,
@@ -58,6 +55,32 @@ struct BatchUnit {
 cudaError_t launch_terms(bool fp32, int team, const void* chat, const TermParams& p, int grid,
                          double* partials, cudaStream_t stream, void* stage = nullptr,
                          double* wstage = nullptr, long long stage_ld = 0);
+
+// One loop hafnian over several sieves (its zero-digit groups, `jobs`, slot matrices in chat_pool
+// at jobs[j].chat_off): the terms are cut into chunks of teams_per_cta(team) terms that never
+// straddle two sieves (job j owns chunks chunk_off[j] .. chunk_off[j+1]-1; its last chunk is
+// padded). CTA c takes chunks k_begin + c + r * grid (r < rounds, below k_end), so the teams of a
+// CTA always share one sieve. Terms outside [tb, te) of the loop hafnian's numbering (jobs[j].base
+// + local index) and padding carry weight 0. With `stage`, chunk k's terms go to columns
+// (k - k_begin) * teams_per_cta + team; without, each team writes its double-double partial:
+// one per team over all its chunks, or (per_chunk) one per chunk and team at that column.
+cudaError_t launch_grouped_terms(bool fp32, int team, const void* chat_pool, const BatchItem* jobs, int n_jobs,
+                                 const long long* chunk_off, long long k_begin, long long k_end, int grid,
+                                 int rounds, unsigned long long tb, unsigned long long te, int team_bytes,
+                                 int items_bytes, double* partials, void* stage, double* wstage,
+                                 long long stage_ld, cudaStream_t stream, int per_chunk = 0);
+int grouped_ctas_per_sm(bool fp32, int team, size_t smem_bytes, bool staged);
+// Staged series of a grouped launch with each column's own degree and border (from its sieve):
+// weighted values (re, 0, im, 0) per column into values. h_max bounds the degrees.
+cudaError_t launch_series_values(bool fp32, const void* stage, const double* wstage, long long count,
+                                 long long stage_ld, const BatchItem* jobs, int n_jobs, const long long* chunk_off,
+                                 long long k_begin, int tpc, int h_max, double* values, cudaStream_t stream);
+// acc[4 * seg_item[s]] += double-double sum of entries seg_begin[s] .. seg_begin[s+1]-1.
+cudaError_t launch_segment_reduce(const double* entries, const long long* seg_begin, const int* seg_item, int n_seg,
+                                  int plain, double* acc, cudaStream_t stream);
+// out[i] = 2^-item_h[i] * acc[i] (item_h < 0: 1; item_h == INT_MAX: NaN).
+cudaError_t launch_item_finalize(const double* acc, const int* item_h, int n_items, double2* out,
+                                 cudaStream_t stream);
 
 // Shared bytes one CTA needs, and CTA size, for a team size.
 int cta_threads(int team);
@@ -82,17 +105,6 @@ cudaError_t launch_reduce(const double* partials, long long count, int h, double
 
 // Batched persistent kernel and its helpers.
 size_t cta_table_bytes(bool fp32, int Hl, int H);
-int batched_ctas_per_sm(bool fp32, int team, size_t smem_bytes);
-cudaError_t launch_batched(bool fp32, int team, const void* chat_pool, const BatchItem* items,
-                           const BatchUnit* units, const int* queue, int n_units, int* next_unit,
-                           double* unit_partials, int team_bytes, int items_bytes, int grid,
-                           cudaStream_t stream, void* stage = nullptr, double* wstage = nullptr);
-// Per loop hafnian i: double-double sum of the partials of units item_unit_begin[i] ..
-// item_unit_begin[i+1]-1 (teams each), written unscaled to out_dd[4 i ..] and scaled by 2^-h to
-// out[i] (either may be NULL).
-cudaError_t launch_batch_reduce(const double* unit_partials, const int* item_unit_begin,
-                                const int* item_h, int teams, int n_items, double2* out,
-                                cudaStream_t stream, double* out_dd = nullptr);
 cudaError_t launch_batch_gather(const double2* B, long long B_stride, const double2* gamma,
                                 long long gamma_stride, int M, const BatchItem* items, int n_items,
                                 double2* chat_pool, float2* chat32_pool, cudaStream_t stream);

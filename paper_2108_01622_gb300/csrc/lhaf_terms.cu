@@ -364,9 +364,9 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
   }
 
   for (unsigned long long rnd = 0; rnd < p.rounds; rnd++) {
-    unsigned long long t = p.t_begin + team_global + rnd * p.total_teams;
-    const bool valid = t < p.t_end;
-    if (!valid) t = p.t_begin;
+    const unsigned long long t_raw = p.t_begin + team_global + rnd * p.total_teams;
+    const bool valid = t_raw >= p.t_lo && t_raw < p.t_end;
+    const unsigned long long t = valid ? t_raw : p.t_begin;  // an idle team repeats a valid term
 
     // ---- digits k_i of the term, delta'_i = eta_i - 2 k_i, and the weight (App. B.4) ----
     // Lane q of the first warp of the team decodes digit q; the weight is a product over lanes.
@@ -663,8 +663,8 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
 
     if constexpr (STAGE) {
       // ---- stage a_m = [t^m] d_M (m = 1..h) and c_m = [t^m](d_M - d_K) (m = 1..h+1) ----
-      if (valid) {
-        const long long col = (long long)(t - p.t_begin);
+      if (valid || p.stage_pad) {
+        const long long col = (long long)(t_raw - p.t_begin);
         const int nc = bord ? 2 * h + 1 : h;
         for (int x = lt; x < nc; x += G) {
           const int m = x < h ? x + 1 : x - h + 1;
@@ -805,197 +805,109 @@ terms_kernel(const typename Cx<R>::t* __restrict__ chat, const __grid_constant__
   }
 }
 
-constexpr int kSeriesThreadsB = 64;
-
-// Series of n staged terms (coefficient-major, ld terms per row), NT threads, one term per thread
-// per round; working arrays in `smem` ([index][thread], (4h + 5) x NT entries). Returns this
-// thread's double-double sum of weight * f in acc (re_hi, re_lo, im_hi, im_lo).
-template <typename R, int NT>
-__device__ __forceinline__ void series_range(const typename Cx<R>::t* __restrict__ st, long long ld,
-                                             const double* __restrict__ ws, long long n, int h, int bord,
-                                             unsigned char* smem, int tid, double* acc) {
-  using V = typename Cx<R>::t;
-  V* SR = reinterpret_cast<V*>(smem);
-  V* Sp = SR + (size_t)(h + 2) * NT;
-  V* Sz = Sp + (size_t)(h + 1) * NT;
-  V* Se = Sz + (size_t)(h + 1) * NT;
-  const V zero = cmake<V>((R)0, (R)0);
-  double rh = 0.0, rl = 0.0, ih = 0.0, il = 0.0;
-  for (long long base = 0; base < n; base += NT) {
-    const long long tt = base + tid;
-    if (tt < n) {
-      auto A = [&](int m) -> V { return st[(long long)(m - 1) * ld + tt]; };
-      auto C = [&](int m) -> V { return bord ? st[(long long)(h + m - 1) * ld + tt] : zero; };
-#define SIDX(i) ((size_t)(i) * NT + tid)
-      SR[SIDX(0)] = zero;
-      SR[SIDX(1)] = C(1);
-      Se[SIDX(0)] = cmake<V>((R)1, (R)0);
-      for (int k = 1; k <= h; k++) {
-        V sR = zero, sp = zero;
-        for (int i = 1; i <= k; i++) {
-          const V ai = A(i);
-          if (bord) cmac(sR, ai, SR[SIDX(k + 1 - i)]);
-          if (i < k) cmac(sp, ai, Sp[SIDX(k - i)]);
-        }
-        const V ck = C(k + 1), ak = A(k);
-        const R kk = (R)k;
-        const V Rk = cmake<V>(ck.x - sR.x, ck.y - sR.y);
-        const V pk = cmake<V>(-rfma(kk, ak.x, sp.x), -rfma(kk, ak.y, sp.y));
-        const V zk = cmake<V>((R)0.5 * rfma(kk, Rk.x, pk.x), (R)0.5 * rfma(kk, Rk.y, pk.y));
-        SR[SIDX(k + 1)] = Rk;
-        Sp[SIDX(k)] = pk;
-        Sz[SIDX(k)] = zk;
-        V se = zero;
-        for (int j = 1; j <= k; j++) cmac(se, Sz[SIDX(j)], Se[SIDX(k - j)]);
-        const R ik = (R)1 / kk;
-        Se[SIDX(k)] = cmake<V>(se.x * ik, se.y * ik);
-      }
-      const V f = Se[SIDX(h)];
-#undef SIDX
-      const double w = ws[tt];
-      dd_add(rh, rl, (double)f.x * w);
-      dd_add(ih, il, (double)f.y * w);
-    }
-  }
-  acc[0] = rh;
-  acc[1] = rl;
-  acc[2] = ih;
-  acc[3] = il;
-}
-
-// ---------------------------------------------------------------------------------------------
-// Batched loop hafnians: a persistent grid pops work units (item, term range) from a queue ordered
-// longest first; all teams of a CTA work on the unit's item (same working dimension, so the
-// teams of a warp stay in step). Each team writes one double-double partial per unit.
-// ---------------------------------------------------------------------------------------------
-template <typename R, int G>
+// One loop hafnian over several sieves (zero-digit groups): chunks of TEAMS terms that stay inside
+// one sieve, taken grid-strided so that each round the CTAs work on neighbouring chunks (similar
+// cost). The CTA copies its chunk's sieve description into shared memory and rebuilds the La Budde
+// tables when the truncation changes.
+template <typename R, int G, bool STAGE>
 __global__ void __launch_bounds__(cta_of(G))
-batched_kernel(const typename Cx<R>::t* __restrict__ chat_pool, const BatchItem* __restrict__ items,
-               const BatchUnit* __restrict__ units, const int* __restrict__ queue, int n_units,
-               int* __restrict__ next_unit, double* __restrict__ unit_partials, int team_bytes,
-               int items_bytes, typename Cx<R>::t* __restrict__ stage, double* __restrict__ wstage) {
+grouped_terms_kernel(const typename Cx<R>::t* __restrict__ chat_pool, const BatchItem* __restrict__ jobs, int n_jobs,
+                     const long long* __restrict__ chunk_off, long long k_begin, long long k_end, int rounds,
+                     unsigned long long tb, unsigned long long te, int team_bytes, int items_bytes,
+                     double* __restrict__ partials, typename Cx<R>::t* __restrict__ stage,
+                     double* __restrict__ wstage, long long stage_ld, int per_chunk) {
+  using V = typename Cx<R>::t;
   constexpr int CTA = cta_of(G);
   constexpr int TEAMS = CTA / G;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TermParams sp;
-  __shared__ int s_q;
-  __shared__ long long s_off, s_stage, s_w;
-  __shared__ int s_staged;
+  __shared__ int s_job, s_Hl;
   const int team = threadIdx.x / G;
   const int lt = threadIdx.x - team * G;
-  for (;;) {
-    if (threadIdx.x == 0) s_q = atomicAdd(next_unit, 1);
+  if (threadIdx.x == 0) {
+    s_job = -1;
+    s_Hl = -1;
+  }
+  double rh = 0.0, rl = 0.0, ih = 0.0, il = 0.0;
+  for (int r = 0; r < rounds; r++) {
+    const long long k = k_begin + blockIdx.x + (long long)r * gridDim.x;
+    if (k >= k_end) break;  // uniform over the CTA
+    // sieve of chunk k: the last j with chunk_off[j] <= k
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (chunk_off[mid] <= k) {
+        lo = mid;
+      } else {
+        hi = mid - 1;
+      }
+    }
+    const int j = lo;
+    __syncthreads();  // the previous chunk is done with sp and the tables
+    if (j != s_job) {
+      // copy the description (a POD of 8-byte words) with all threads
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&jobs[j].p);
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sp);
+      for (int w = threadIdx.x; w < (int)(sizeof(TermParams) / 8); w += CTA) dst[w] = src[w];
+    }
     __syncthreads();
-    const int q = s_q;
-    if (q >= n_units) break;
-    const int u = queue[q];
+    const bool valid_desc = sp.nd >= 2 && sp.nd <= kMaxDim && sp.P <= kMaxPairs && sp.h <= kMaxDegree &&
+                            sp.Hl <= sp.nd && sp.n_items == sp.Hl * (sp.Hl - 1) / 2;
+    if (!valid_desc) continue;  // a description outside the compiled limits is skipped
+    if (j != s_job || sp.Hl != s_Hl) {
+      build_cta_tables<R, CTA>(sp, smem);
+      __syncthreads();
+    }
     if (threadIdx.x == 0) {
-      const BatchUnit un = units[u];
-      sp = items[un.item].p;
-      s_off = items[un.item].chat_off;
-      s_stage = un.stage_off;  // per-CTA region size (elements), or -1 for an inline unit
-      s_w = un.w_off;          // per-CTA weight region size
-      s_staged = (stage != nullptr && un.stage_off >= 0) ? 1 : 0;
-      sp.t_begin = un.t0;
-      sp.t_end = un.t1;
+      // chunk terms t0 .. t0 + TEAMS - 1 of sieve j; valid below its term count (jobs[j].p.t_end)
+      // and inside [tb, te) of the loop hafnian's numbering
+      const unsigned long long t0 = (unsigned long long)(k - chunk_off[j]) * TEAMS;
+      const unsigned long long base = jobs[j].base, T = jobs[j].p.t_end;
+      unsigned long long hi = T < t0 + TEAMS ? T : t0 + TEAMS;
+      if (te <= base) {
+        hi = t0;
+      } else if (te - base < hi) {
+        hi = te - base;
+      }
+      sp.t_begin = t0;
+      sp.t_end = hi > t0 ? hi : t0;
+      sp.t_lo = tb > base ? tb - base : 0ull;
+      sp.rounds = 1;
       sp.total_teams = TEAMS;
-      sp.rounds = (un.t1 - un.t0 + TEAMS - 1) / TEAMS;
       sp.team_bytes = team_bytes;
       sp.items_bytes = items_bytes;
+      sp.stage_pad = STAGE ? 1 : 0;
+      s_job = j;
+      s_Hl = sp.Hl;
     }
-    __syncthreads();
-    // a descriptor outside the compiled limits is skipped (its partials stay as they are)
-    if (sp.nd < 2 || sp.nd > kMaxDim || sp.P > kMaxPairs || sp.h > kMaxDegree || sp.Hl > sp.nd ||
-        sp.n_items != sp.Hl * (sp.Hl - 1) / 2)
-      continue;
-    build_cta_tables<R, CTA>(sp, smem);
     __syncthreads();
     double acc[4];
-    if (s_staged) {
-      // The unit's polynomials go to this CTA's staging region; then the CTA's threads finish them
-      // one term per thread (working arrays over the team area of shared memory) and the CTA's
-      // double-double sum becomes the unit's partial (first team slot; the others are zeroed).
-      const long long n = (long long)(sp.t_end - sp.t_begin);
-      typename Cx<R>::t* cst = stage + s_stage * (long long)blockIdx.x;
-      double* cw = wstage + s_w * (long long)blockIdx.x;
-      sieve_terms<R, G, true>(chat_pool + s_off, sp, smem, (unsigned long long)team, cst, cw, n, acc);
-      __syncthreads();
-      series_range<R, CTA>(cst, n, cw, n, sp.h, sp.bord, smem + items_bytes, threadIdx.x, acc);
-      __shared__ double red[4][CTA];
-      red[0][threadIdx.x] = acc[0];
-      red[1][threadIdx.x] = acc[1];
-      red[2][threadIdx.x] = acc[2];
-      red[3][threadIdx.x] = acc[3];
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
-        for (int x = 0; x < CTA; x++) {
-          dd_add_dd(a, b, red[0][x], red[1][x]);
-          dd_add_dd(c, d, red[2][x], red[3][x]);
+    const long long colbase = (k - k_begin) * TEAMS;
+    sieve_terms<R, G, STAGE>(reinterpret_cast<const V*>(chat_pool) + jobs[j].chat_off, sp, smem,
+                             (unsigned long long)team, STAGE ? stage + colbase : nullptr,
+                             STAGE ? wstage + colbase : nullptr, stage_ld, acc);
+    if constexpr (!STAGE) {
+      if (per_chunk) {
+        if (lt == 0) {
+          double* o = partials + 4ll * (colbase + team);
+          o[0] = acc[0];
+          o[1] = acc[1];
+          o[2] = acc[2];
+          o[3] = acc[3];
         }
-        for (int tm = 0; tm < TEAMS; tm++) {
-          double* o = unit_partials + 4ll * ((long long)u * TEAMS + tm);
-          o[0] = tm == 0 ? a : 0.0;
-          o[1] = tm == 0 ? b : 0.0;
-          o[2] = tm == 0 ? c : 0.0;
-          o[3] = tm == 0 ? d : 0.0;
-        }
-      }
-    } else {
-      sieve_terms<R, G, false>(chat_pool + s_off, sp, smem, (unsigned long long)team, nullptr, nullptr, 0, acc);
-      if (lt == 0) {
-        double* o = unit_partials + 4ll * ((long long)u * TEAMS + team);
-        o[0] = acc[0];
-        o[1] = acc[1];
-        o[2] = acc[2];
-        o[3] = acc[3];
+      } else {
+        dd_add_dd(rh, rl, acc[0], acc[1]);
+        dd_add_dd(ih, il, acc[2], acc[3]);
       }
     }
-    __syncthreads();
   }
-}
-
-// One warp per item: double-double sum of its units' team partials, then 2^-h (Eq. fdsieve).
-// h < 0 marks an empty pattern (lhaf = 1); h == INT_MAX marks an item that was not computed.
-__global__ void __launch_bounds__(128)
-batch_reduce_kernel(const double* __restrict__ unit_partials, const int* __restrict__ item_unit_begin,
-                    const int* __restrict__ item_h, int teams, int n_items, double2* __restrict__ out,
-                    double* __restrict__ out_dd) {
-  const int item = blockIdx.x * 4 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (item >= n_items) return;
-  const long long b = (long long)item_unit_begin[item] * teams, e = (long long)item_unit_begin[item + 1] * teams;
-  double rh = 0.0, rl = 0.0, ih = 0.0, il = 0.0;
-  for (long long i = b + lane; i < e; i += 32) {
-    dd_add_dd(rh, rl, unit_partials[4 * i + 0], unit_partials[4 * i + 1]);
-    dd_add_dd(ih, il, unit_partials[4 * i + 2], unit_partials[4 * i + 3]);
-  }
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) {
-    const double a = __shfl_xor_sync(0xffffffffu, rh, off), bb = __shfl_xor_sync(0xffffffffu, rl, off);
-    const double c = __shfl_xor_sync(0xffffffffu, ih, off), d = __shfl_xor_sync(0xffffffffu, il, off);
-    dd_add_dd(rh, rl, a, bb);
-    dd_add_dd(ih, il, c, d);
-  }
-  if (lane == 0) {
-    const int h = item_h[item];
-    if (out_dd) {
-      double* o = out_dd + 4ll * item;
+  if constexpr (!STAGE) {
+    if (lt == 0 && !per_chunk) {
+      double* o = partials + 4ull * ((unsigned long long)blockIdx.x * TEAMS + team);
       o[0] = rh;
       o[1] = rl;
       o[2] = ih;
       o[3] = il;
-    }
-    if (out) {
-      if (h < 0) {
-        out[item] = make_double2(1.0, 0.0);
-      } else if (h == 0x7fffffff) {
-        out[item] =
-            make_double2(__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll));
-      } else {
-        const double s1 = __longlong_as_double((long long)(1023 - h) << 52);
-        out[item] = make_double2((rh + rl) * s1, (ih + il) * s1);
-      }
     }
   }
 }
@@ -1331,6 +1243,132 @@ cudaError_t launch_terms(bool fp32, int team, const void* chat, const TermParams
   return cudaLaunchKernel(k, dim3(grid), dim3(cta_of(team)), args, smem, stream);
 }
 
+// Series of the staged terms of a grouped launch, one term per thread, each with its own sieve's
+// degree and border (column col belongs to chunk k_begin + col / tpc of sieve j, found in
+// chunk_off): writes the weighted value (re, 0, im, 0) of every column to values, for a per-item
+// reduction afterwards. Working arrays in shared memory for the largest degree h_max.
+template <typename R>
+__global__ void __launch_bounds__(kSeriesThreads)
+series_values_kernel(const typename Cx<R>::t* __restrict__ stage, const double* __restrict__ wstage, long long count,
+                     long long stage_ld, const BatchItem* __restrict__ jobs, int n_jobs,
+                     const long long* __restrict__ chunk_off, long long k_begin, int tpc, int h_max,
+                     double* __restrict__ values) {
+  using V = typename Cx<R>::t;
+  extern __shared__ __align__(16) unsigned char smem[];
+  V* SR = reinterpret_cast<V*>(smem);                 // (h_max + 2) x threads
+  V* Sp = SR + (size_t)(h_max + 2) * kSeriesThreads;  // (h_max + 1) x threads
+  V* Sz = Sp + (size_t)(h_max + 1) * kSeriesThreads;
+  V* Se = Sz + (size_t)(h_max + 1) * kSeriesThreads;
+  const int tid = threadIdx.x;
+  const long long tt = (long long)blockIdx.x * kSeriesThreads + tid;
+  if (tt >= count) return;
+  const long long k = k_begin + tt / tpc;
+  int lo = 0, hi = n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (chunk_off[mid] <= k) {
+      lo = mid;
+    } else {
+      hi = mid - 1;
+    }
+  }
+  const int h = jobs[lo].p.h, bord = jobs[lo].p.bord;
+  const V zero = cmake<V>((R)0, (R)0);
+  double fr = 0.0, fi = 0.0;
+  if (h >= 1 && h <= h_max) {
+    auto A = [&](int m) -> V { return stage[(long long)(m - 1) * stage_ld + tt]; };
+    auto C = [&](int m) -> V { return bord ? stage[(long long)(h + m - 1) * stage_ld + tt] : zero; };
+#define SIDX(i) ((size_t)(i) * kSeriesThreads + tid)
+    SR[SIDX(0)] = zero;
+    SR[SIDX(1)] = C(1);
+    Se[SIDX(0)] = cmake<V>((R)1, (R)0);
+    for (int kk_ = 1; kk_ <= h; kk_++) {
+      V sR = zero, sp = zero;
+      for (int i = 1; i <= kk_; i++) {
+        const V ai = A(i);
+        if (bord) cmac(sR, ai, SR[SIDX(kk_ + 1 - i)]);
+        if (i < kk_) cmac(sp, ai, Sp[SIDX(kk_ - i)]);
+      }
+      const V ck = C(kk_ + 1), ak = A(kk_);
+      const R kk = (R)kk_;
+      const V Rk = cmake<V>(ck.x - sR.x, ck.y - sR.y);
+      const V pk = cmake<V>(-rfma(kk, ak.x, sp.x), -rfma(kk, ak.y, sp.y));
+      const V zk = cmake<V>((R)0.5 * rfma(kk, Rk.x, pk.x), (R)0.5 * rfma(kk, Rk.y, pk.y));
+      SR[SIDX(kk_ + 1)] = Rk;
+      Sp[SIDX(kk_)] = pk;
+      Sz[SIDX(kk_)] = zk;
+      V se = zero;
+      for (int j = 1; j <= kk_; j++) cmac(se, Sz[SIDX(j)], Se[SIDX(kk_ - j)]);
+      const R ik = (R)1 / kk;
+      Se[SIDX(kk_)] = cmake<V>(se.x * ik, se.y * ik);
+    }
+    const V f = Se[SIDX(h)];
+#undef SIDX
+    const double w = wstage[tt];
+    fr = (double)f.x * w;
+    fi = (double)f.y * w;
+  }
+  double* o = values + 4ll * tt;
+  o[0] = fr;
+  o[1] = 0.0;
+  o[2] = fi;
+  o[3] = 0.0;
+}
+
+// Per segment s: double-double sum of entries seg_begin[s] .. seg_begin[s+1]-1 (4 doubles each),
+// added to acc[4 * seg_item[s]] (one warp per segment; segments of one launch name distinct items).
+__global__ void __launch_bounds__(128)
+segment_reduce_kernel(const double* __restrict__ entries, const long long* __restrict__ seg_begin,
+                      const int* __restrict__ seg_item, int n_seg, int plain, double* __restrict__ acc) {
+  const int sg = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (sg >= n_seg) return;
+  const long long b = seg_begin[sg], e = seg_begin[sg + 1];
+  double rh = 0.0, rl = 0.0, ih = 0.0, il = 0.0;
+  for (long long i = b + lane; i < e; i += 32) {
+    if (plain) {
+      rh += entries[4 * i + 0];
+      ih += entries[4 * i + 2];
+    } else {
+      dd_add_dd(rh, rl, entries[4 * i + 0], entries[4 * i + 1]);
+      dd_add_dd(ih, il, entries[4 * i + 2], entries[4 * i + 3]);
+    }
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    const double a = __shfl_xor_sync(0xffffffffu, rh, off), bb = __shfl_xor_sync(0xffffffffu, rl, off);
+    const double c = __shfl_xor_sync(0xffffffffu, ih, off), d = __shfl_xor_sync(0xffffffffu, il, off);
+    dd_add_dd(rh, rl, a, bb);
+    dd_add_dd(ih, il, c, d);
+  }
+  if (lane == 0) {
+    double* o = acc + 4ll * seg_item[sg];
+    double h0 = o[0], l0 = o[1], h1 = o[2], l1 = o[3];
+    dd_add_dd(h0, l0, rh, rl);
+    dd_add_dd(h1, l1, ih, il);
+    o[0] = h0;
+    o[1] = l0;
+    o[2] = h1;
+    o[3] = l1;
+  }
+}
+
+// out[i] = 2^-h_i * acc[i] (h < 0: empty pattern, 1; h == INT_MAX: not computed, NaN).
+__global__ void item_finalize_kernel(const double* __restrict__ acc, const int* __restrict__ item_h, int n_items,
+                                     double2* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_items) return;
+  const int h = item_h[i];
+  if (h < 0) {
+    out[i] = make_double2(1.0, 0.0);
+  } else if (h == 0x7fffffff) {
+    out[i] = make_double2(__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll));
+  } else {
+    const double s1 = __longlong_as_double((long long)(1023 - h) << 52);
+    out[i] = make_double2((acc[4 * i] + acc[4 * i + 1]) * s1, (acc[4 * i + 2] + acc[4 * i + 3]) * s1);
+  }
+}
+
 size_t series_shared_bytes(bool fp32, int h) {
   const size_t cs = fp32 ? sizeof(float2) : sizeof(double2);
   return (size_t)(4 * h + 5) * kSeriesThreads * cs;
@@ -1348,6 +1386,35 @@ cudaError_t launch_series(bool fp32, const void* stage, const double* wstage, lo
   void* args[] = {(void*)&stage, (void*)&wstage, (void*)&count, (void*)&stage_ld, (void*)&h,
                   (void*)&bord,  (void*)&plain,  (void*)&partials};
   return cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(kSeriesThreads), args, smem, stream);
+}
+
+cudaError_t launch_series_values(bool fp32, const void* stage, const double* wstage, long long count,
+                                 long long stage_ld, const BatchItem* jobs, int n_jobs, const long long* chunk_off,
+                                 long long k_begin, int tpc, int h_max, double* values, cudaStream_t stream) {
+  if (count <= 0) return cudaSuccess;
+  const size_t smem = series_shared_bytes(fp32, h_max);
+  const void* k = fp32 ? (const void*)series_values_kernel<float> : (const void*)series_values_kernel<double>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long blocks = series_blocks(count);
+  void* args[] = {(void*)&stage,    (void*)&wstage,  (void*)&count, (void*)&stage_ld,
+                  (void*)&jobs,     (void*)&n_jobs,  (void*)&chunk_off, (void*)&k_begin,
+                  (void*)&tpc,      (void*)&h_max,   (void*)&values};
+  return cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(kSeriesThreads), args, smem, stream);
+}
+
+cudaError_t launch_segment_reduce(const double* entries, const long long* seg_begin, const int* seg_item, int n_seg,
+                                  int plain, double* acc, cudaStream_t stream) {
+  if (n_seg <= 0) return cudaSuccess;
+  segment_reduce_kernel<<<(n_seg + 3) / 4, 128, 0, stream>>>(entries, seg_begin, seg_item, n_seg, plain, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_item_finalize(const double* acc, const int* item_h, int n_items, double2* out,
+                                 cudaStream_t stream) {
+  if (n_items <= 0) return cudaSuccess;
+  item_finalize_kernel<<<(n_items + 127) / 128, 128, 0, stream>>>(acc, item_h, n_items, out);
+  return cudaGetLastError();
 }
 
 size_t cta_table_bytes(bool fp32, int Hl, int H) { return items_bytes_of(fp32, Hl, H); }
@@ -1406,21 +1473,43 @@ cudaError_t launch_grad_reduce(const double2* gpart, long long teams, int len, i
   return cudaGetLastError();
 }
 
-template <typename R, int G> static const void* bptr() { return (const void*)batched_kernel<R, G>; }
+cudaError_t launch_batch_gather(const double2* B, long long B_stride, const double2* gamma, long long gamma_stride,
+                                int M, const BatchItem* items, int n_items, double2* chat_pool, float2* chat32_pool,
+                                cudaStream_t stream) {
+  if (n_items <= 0) return cudaSuccess;
+  batch_gather_kernel<<<n_items, 256, 0, stream>>>(B, B_stride, gamma, gamma_stride, M, items, chat_pool, chat32_pool);
+  return cudaGetLastError();
+}
 
-static const void* pick_batched(bool fp32, int team) {
-  switch (team) {
-    case 8: return fp32 ? bptr<float, 8>() : bptr<double, 8>();
-    case 16: return fp32 ? bptr<float, 16>() : bptr<double, 16>();
-    case 32: return fp32 ? bptr<float, 32>() : bptr<double, 32>();
-    case 64: return fp32 ? bptr<float, 64>() : bptr<double, 64>();
-    case 128: return fp32 ? bptr<float, 128>() : bptr<double, 128>();
+template <typename R, int G, bool S> static const void* gkptr() { return (const void*)grouped_terms_kernel<R, G, S>; }
+
+template <bool S> static const void* pick_grouped_s(bool fp32, int team) {
+  if (fp32) {
+    switch (team) {
+      case 8: return gkptr<float, 8, S>();
+      case 16: return gkptr<float, 16, S>();
+      case 32: return gkptr<float, 32, S>();
+      case 64: return gkptr<float, 64, S>();
+      case 128: return gkptr<float, 128, S>();
+    }
+  } else {
+    switch (team) {
+      case 8: return gkptr<double, 8, S>();
+      case 16: return gkptr<double, 16, S>();
+      case 32: return gkptr<double, 32, S>();
+      case 64: return gkptr<double, 64, S>();
+      case 128: return gkptr<double, 128, S>();
+    }
   }
   return nullptr;
 }
 
-int batched_ctas_per_sm(bool fp32, int team, size_t smem_bytes) {
-  const void* k = pick_batched(fp32, team);
+static const void* pick_grouped(bool fp32, int team, bool staged) {
+  return staged ? pick_grouped_s<true>(fp32, team) : pick_grouped_s<false>(fp32, team);
+}
+
+int grouped_ctas_per_sm(bool fp32, int team, size_t smem_bytes, bool staged) {
+  const void* k = pick_grouped(fp32, team, staged);
   if (!k) return 0;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -1434,34 +1523,22 @@ int batched_ctas_per_sm(bool fp32, int team, size_t smem_bytes) {
   return n;
 }
 
-cudaError_t launch_batched(bool fp32, int team, const void* chat_pool, const BatchItem* items, const BatchUnit* units,
-                           const int* queue, int n_units, int* next_unit, double* unit_partials, int team_bytes,
-                           int items_bytes, int grid, cudaStream_t stream, void* stage, double* wstage) {
-  const void* k = pick_batched(fp32, team);
-  if (!k) return cudaErrorInvalidValue;
+cudaError_t launch_grouped_terms(bool fp32, int team, const void* chat_pool, const BatchItem* jobs, int n_jobs,
+                                 const long long* chunk_off, long long k_begin, long long k_end, int grid,
+                                 int rounds, unsigned long long tb, unsigned long long te, int team_bytes,
+                                 int items_bytes, double* partials, void* stage, double* wstage,
+                                 long long stage_ld, cudaStream_t stream, int per_chunk) {
+  const bool staged = stage != nullptr;
+  const void* k = pick_grouped(fp32, team, staged);
+  if (!k || grid <= 0 || n_jobs <= 0) return cudaErrorInvalidValue;
   const size_t smem = (size_t)items_bytes + (size_t)teams_per_cta(team) * team_bytes;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  void* args[] = {(void*)&chat_pool,     (void*)&items,      (void*)&units,       (void*)&queue,
-                  (void*)&n_units,       (void*)&next_unit,  (void*)&unit_partials, (void*)&team_bytes,
-                  (void*)&items_bytes,   (void*)&stage,      (void*)&wstage};
+  void* args[] = {(void*)&chat_pool, (void*)&jobs,       (void*)&n_jobs,    (void*)&chunk_off,
+                  (void*)&k_begin,   (void*)&k_end,      (void*)&rounds,    (void*)&tb,
+                  (void*)&te,        (void*)&team_bytes, (void*)&items_bytes, (void*)&partials,
+                  (void*)&stage,     (void*)&wstage,     (void*)&stage_ld, (void*)&per_chunk};
   return cudaLaunchKernel(k, dim3(grid), dim3(cta_of(team)), args, smem, stream);
-}
-
-cudaError_t launch_batch_reduce(const double* unit_partials, const int* item_unit_begin, const int* item_h, int teams,
-                                int n_items, double2* out, cudaStream_t stream, double* out_dd) {
-  if (n_items <= 0) return cudaSuccess;
-  batch_reduce_kernel<<<(n_items + 3) / 4, 128, 0, stream>>>(unit_partials, item_unit_begin, item_h, teams, n_items,
-                                                             out, out_dd);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_batch_gather(const double2* B, long long B_stride, const double2* gamma, long long gamma_stride,
-                                int M, const BatchItem* items, int n_items, double2* chat_pool, float2* chat32_pool,
-                                cudaStream_t stream) {
-  if (n_items <= 0) return cudaSuccess;
-  batch_gather_kernel<<<n_items, 256, 0, stream>>>(B, B_stride, gamma, gamma_stride, M, items, chat_pool, chat32_pool);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const double* partials, long long count, int h, double* out_dd, double2* out_val,

@@ -184,6 +184,33 @@ def test_zero_digit_range_partials_cross_groups(ctx, lg):
         ctx.lhaf_range(p.B, p.gamma, p.reps, 0, T + 1)
 
 
+@pytest.mark.parametrize("loops", [False, True])
+def test_zero_digit_groups_inline_series(ctx, lg, loops):
+    # h = 25 > the staged-series limit: the groups finish their series inside the team. Repeat
+    # counts 6-7 make the signed sum cancel by ~1e8 (sum |terms| / |lhaf|), beyond what an FP64
+    # sum can resolve to 1e-10, so the reference is the oracle in extended precision and the bar
+    # is the forward error of the sum: 1e-13 * sum |terms| * 2^-h (each term carries a relative
+    # error of order 1e-15; measured about 1e-15).
+    reps = (7, 7, 6, 6, 6, 6, 6, 6)
+    p = wl.small_problem(seed=77, M=len(reps), reps=reps, loops=loops)
+    ref = complex(lo.lhaf_repeated(p.B, p.gamma, p.reps, dtype=np.clongdouble))
+    scale = sum(abs(t) for t in lo.repeated_sieve_terms(p.B, p.gamma, p.reps)) / 2.0 ** 25
+    got, st = ctx.lhaf(p.B, p.gamma, p.reps, stats=True)
+    full = ctx.lhaf(p.B, p.gamma, p.reps, flags=lg.NO_ZERO_SPLIT)
+    assert st["h"] == 25 and lg.plan_groups(reps) == 8
+    assert abs(got - ref) <= 1e-13 * scale and abs(full - ref) <= 1e-13 * scale
+
+
+def test_inline_series_well_conditioned(ctx, lg):
+    # h = 25 with single repeats over two modes: 13 terms, no zero-digit split
+    reps = (25, 25)
+    p = wl.small_problem(seed=5, M=2, reps=reps, loops=True)
+    ref = lo.lhaf_repeated(p.B, p.gamma, p.reps)
+    got, st = ctx.lhaf(p.B, p.gamma, p.reps, stats=True)
+    assert st["h"] == 25 and lg.plan_groups(reps) == 0
+    assert rel(got, ref) < TOL
+
+
 def test_zero_digit_groups_device_pointers_and_fp32(ctx, lg):
     import torch
 
