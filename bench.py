@@ -30,7 +30,7 @@ METRIC = "lhaf sieve terms/s (collision-pattern loop hafnian, FP64)"
 UNIT = "terms/s"
 WORKLOAD = ("collision-pattern loop hafnian: 100-mode Haar interferometer, r ~ U[1.0,1.6], gamma = 0, "
             "40 photons over 22 modes with counts 1..4 (seeded multinomial), complex128, repeated-pair sieve")
-KERNEL_NAME = "batched_kernel (FP64 sieve terms of the zero-digit groups, persistent)"
+KERNEL_NAME = "grouped_terms_kernel (FP64 sieve terms of the zero-digit groups)"
 NOMINAL_FP64_GFLOPS = 152 * 4 * 0.5 * 2 * 2.070  # SMs x sub-partitions x FMA lanes/clk x 2 flops x GHz
 
 

@@ -335,28 +335,6 @@ int pick_team(lhaf_ctx* ctx, bool fp32, const Plan& pl, bool staged, int family,
 
 namespace {
 
-// Build the slot matrix into ctx->d_chat (and d_chat32 for FP32 terms).
-lhaf_status stage_chat(lhaf_ctx* ctx, const Plan& pl, int M, const lhaf_c128* B, const lhaf_c128* gamma,
-                       uint32_t flags, bool fp32) {
-  const int nd = pl.nd;
-  if (flags & LHAF_DEVICE_PTRS) {
-    cudaError_t e = launch_gather((const double2*)B, (const double2*)gamma, M, pl.slot_mode.data(), pl.P, pl.bord,
-                                  ctx->d_chat, fp32 ? ctx->d_chat32 : nullptr, ctx->stream);
-    return e == cudaSuccess ? LHAF_OK : LHAF_ECUDA;
-  }
-  build_chat_host(pl, M, B, gamma, (std::complex<double>*)ctx->h_chat);
-  cudaError_t e;
-  if (fp32) {
-    for (int i = 0; i < nd * nd; i++) ctx->h_chat32[i] = make_float2((float)ctx->h_chat[i].x, (float)ctx->h_chat[i].y);
-    e = cudaMemcpyAsync(ctx->d_chat32, ctx->h_chat32, (size_t)nd * nd * sizeof(float2), cudaMemcpyHostToDevice,
-                        ctx->stream);
-  } else {
-    e = cudaMemcpyAsync(ctx->d_chat, ctx->h_chat, (size_t)nd * nd * sizeof(double2), cudaMemcpyHostToDevice,
-                        ctx->stream);
-  }
-  return e == cudaSuccess ? LHAF_OK : LHAF_ECUDA;
-}
-
 bool has_loops_host(const Plan& pl, int M, const lhaf_c128* B, const lhaf_c128* gamma) {
   for (int s = 0; s < 2 * pl.P; s++) {
     const int m = pl.slot_mode[s];
@@ -409,89 +387,6 @@ bool lhafgpu::ensure_stage(lhaf_ctx* ctx, size_t bytes, size_t terms) {
 
 namespace {
 
-// Runs the sieve over [tb, te) of the plan; writes the dd partial (unscaled) and/or the scaled
-// value into device buffers dd_dst / val_dst. Degrees up to kStageMaxDegree stage the term
-// polynomials and finish them one term per thread (series_kernel), in chunks of term ranges that
-// fit the staging buffer; larger degrees finish each term inside the term kernel.
-lhaf_status run_terms(lhaf_ctx* ctx, const Plan& pl, uint32_t flags, uint64_t tb, uint64_t te, double* dd_dst,
-                      double2* val_dst, lhaf_stats* stats, bool timed) {
-  const bool fp32 = (flags & LHAF_FP32_TERMS) != 0;
-  const char* env_stage = std::getenv("LHAF_STAGE");
-  bool staged = pl.h <= kStageMaxDegree && !(env_stage && env_stage[0] == '0');
-  const size_t cs = fp32 ? sizeof(float2) : sizeof(double2);
-  const int rows = pl.bord ? 2 * pl.h + 1 : pl.h;
-  const uint64_t T = te > tb ? te - tb : 0;
-  uint64_t chunk = T;
-  if (staged) {
-    const uint64_t cap = kStageBytesMax / ((size_t)rows * cs);
-    chunk = std::min<uint64_t>(T, cap);
-    const uint64_t series_cap = (uint64_t)ctx->partial_cap * 64;  // series blocks of 64 terms
-    chunk = std::min<uint64_t>(chunk, series_cap);
-    if (chunk < 1) chunk = 1;
-    if (!ensure_stage(ctx, (size_t)rows * cs * chunk, chunk)) staged = false;
-    if (!staged) chunk = T;
-  }
-  int occ = 0;
-  const void* chat = fp32 ? (const void*)ctx->d_chat32 : (const void*)ctx->d_chat;
-  const int team = pick_team(ctx, fp32, pl, staged, 0, chat, &occ);
-  if (team == 0) return LHAF_ETOOBIG;
-  occ = ctas_per_sm_override(occ);
-  TermParams p;
-  fill_params(pl, fp32, staged, team, flags, p);
-  const int tpc = teams_per_cta(team);
-  const uint64_t max_ctas = (uint64_t)ctx->sms * (uint64_t)occ;
-  double* acc_dd = dd_dst ? dd_dst : ctx->d_out;  // running double-double sum over chunks
-  if (timed) cudaEventRecord(ctx->ev0, ctx->stream);
-  uint64_t c0 = tb;
-  int ci = 0, launches = 0;
-  do {
-    const uint64_t c1 = std::min<uint64_t>(te, c0 + chunk);
-    const uint64_t n = c1 - c0;
-    const uint64_t grid = balanced_grid(n, tpc, max_ctas, &p.rounds);
-    p.total_teams = grid * (uint64_t)tpc;
-    if (!staged && p.total_teams > ctx->partial_cap) return LHAF_ETOOBIG;
-    p.t_begin = c0;
-    p.t_end = c1;
-    cudaError_t e;
-    long long nparts;
-    if (n == 0) {
-      nparts = 0;  // empty range: the reduction writes a zero partial
-    } else if (staged) {
-      e = launch_terms(fp32, team, chat, p, (int)grid, ctx->d_partials, ctx->stream, ctx->d_stage, ctx->d_wstage,
-                       (long long)chunk);
-      if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "terms kernel");
-      e = launch_series(fp32, ctx->d_stage, ctx->d_wstage, (long long)n, (long long)chunk, pl.h, pl.bord, p.plain,
-                        ctx->d_partials, ctx->stream);
-      if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "series kernel");
-      nparts = series_blocks((long long)n);
-      launches += 2;
-    } else {
-      e = launch_terms(fp32, team, chat, p, (int)grid, ctx->d_partials, ctx->stream);
-      if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "terms kernel");
-      nparts = (long long)p.total_teams;
-      launches += 1;
-    }
-    const bool last = c1 >= te;
-    e = launch_reduce(ctx->d_partials, nparts, pl.h, acc_dd, last ? val_dst : nullptr, ctx->stream, ci > 0 ? 1 : 0);
-    if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "reduction kernel");
-    launches += 1;
-    c0 = c1;
-    ci++;
-  } while (c0 < te);
-  if (timed) cudaEventRecord(ctx->ev1, ctx->stream);
-  if (stats) {
-    stats->terms = T;
-    stats->n_dim = pl.nd;
-    stats->h = pl.h;
-    stats->pairs = pl.P;
-    stats->team = team;
-    stats->flops_model = (double)T * lhaf_model_flops_per_term(pl.nd, pl.h, pl.bord);
-    stats->kernel_ms = 0.0;
-    stats->launches = launches;
-  }
-  return LHAF_OK;
-}
-
 // One loop hafnian over its zero-digit groups `subs` (numbered group after group), restricted to
 // [tb, te): grid-strided chunks that never straddle two groups (grouped_terms_kernel), then, for
 // degrees up to kStageMaxDegree, the staged series one term per thread; both in launches sized to
@@ -515,7 +410,8 @@ lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& 
     return (lhaf_status)record_cuda(cudaPeekAtLastError(), "cudaEventCreate");
   }
   const int nj = (int)subs.size();
-  if (!w.h_items.reserve(sizeof(BatchItem) * nj) || !w.items.reserve(sizeof(BatchItem) * nj) ||
+  if (!w.counter.reserve(sizeof(unsigned long long)) || !w.h_items.reserve(sizeof(BatchItem) * nj) ||
+      !w.items.reserve(sizeof(BatchItem) * nj) ||
       !w.h_chunks.reserve(sizeof(long long) * (nj + 1)) || !w.chunks.reserve(sizeof(long long) * (nj + 1)))
     return LHAF_ENOMEM;
   BatchItem* jobs = static_cast<BatchItem*>(w.h_items.p);
@@ -630,11 +526,14 @@ lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& 
       unsigned long long rounds = 1;
       const uint64_t grid = balanced_grid((uint64_t)n, 1, max_ctas, &rounds);
       if (!staged && grid * (uint64_t)tpc > ctx->partial_cap) return LHAF_ETOOBIG;
+      if (cudaMemsetAsync(w.counter.p, 0, sizeof(unsigned long long), s) != cudaSuccess)
+        return (lhaf_status)record_cuda(cudaPeekAtLastError(), "chunk queue reset");
       cudaError_t e = launch_grouped_terms(fp32, team, pool_ptr, (const BatchItem*)w.items.p, nj,
                                            (const long long*)w.chunks.p, c0, c1, (int)grid, (int)rounds, tb, te,
                                            (int)team_bytes, (int)items_bytes, ctx->d_partials,
                                            staged ? ctx->d_stage : nullptr, staged ? ctx->d_wstage : nullptr,
-                                           staged ? (long long)cap_cols : 0, s);
+                                           staged ? (long long)cap_cols : 0, s, 0,
+                                           (unsigned long long*)w.counter.p);
       if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "grouped terms kernel");
       launches++;
       if (staged) {
@@ -735,17 +634,9 @@ lhaf_status lhaf_common(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c12
   const bool timed = stats != nullptr;
   double* dd_dst = ranged ? (dev ? partial_dd : ctx->d_out) : nullptr;
   double2* val_dst = ranged ? nullptr : (dev ? (double2*)out : (double2*)(ctx->d_out + 4));
-  if (split) {
-    st = run_grouped(ctx, pl, subs, M, B, gamma, flags, dev, tb, te, dd_dst, val_dst, stats, timed);
-  } else {
-    st = stage_chat(ctx, pl, M, B, gamma, flags, fp32);
-    if (st != LHAF_OK) return st;
-    st = run_terms(ctx, pl, flags, tb, te, dd_dst, val_dst, stats, timed);
-    if (st == LHAF_OK && stats) {
-      if (dev) stats->launches += 1;  // slot-matrix gather
-      stats->h2d_bytes = dev ? 0 : (uint64_t)pl.nd * pl.nd * (fp32 ? sizeof(float2) : sizeof(double2));
-    }
-  }
+  (void)fp32;
+  if (!split) subs.assign(1, pl);  // one sieve on the full working matrix
+  st = run_grouped(ctx, pl, subs, M, B, gamma, flags, dev, tb, te, dd_dst, val_dst, stats, timed);
   if (st != LHAF_OK) return st;
   if (stats) stats->d2h_bytes = dev ? 0 : 6 * sizeof(double);
   if (!dev) {

@@ -175,7 +175,8 @@ lhaf_status prepare_batch(lhaf_ctx* ctx, BatchWork& w, int batch, int M, const l
 
   // ---- descriptors and slot-matrix pool, class after class ----
   const int n_desc = std::max(n_jobs, 1);
-  if (!w.h_items.reserve(sizeof(BatchItem) * n_desc) || !w.items.reserve(sizeof(BatchItem) * n_desc) ||
+  if (!w.counter.reserve(sizeof(unsigned long long)) || !w.h_items.reserve(sizeof(BatchItem) * n_desc) ||
+      !w.items.reserve(sizeof(BatchItem) * n_desc) ||
       !w.h_item_h.reserve(sizeof(int) * batch) || !w.item_h.reserve(sizeof(int) * batch) ||
       !w.acc.reserve(sizeof(double) * 4 * batch) || !w.out.reserve(sizeof(double2) * batch) ||
       !w.h_out.reserve(sizeof(double2) * batch))
@@ -387,11 +388,13 @@ lhaf_status enqueue_batch(BatchWork& w, const BatchLaunch& L, double2* out, cuda
     const BatchItem* cj = items + cl.desc_off;
     const long long* cc = chunks + cl.chunk_off;
     for (const GLaunch& lg : cl.launches) {
+      if (cudaMemsetAsync(w.counter.p, 0, sizeof(unsigned long long), s) != cudaSuccess)
+        return (lhaf_status)record_cuda(cudaPeekAtLastError(), "chunk queue reset");
       cudaError_t e = launch_grouped_terms(
           L.fp32, cl.team, pool_ptr, cj, cl.n_jobs, cc, lg.c0, lg.c1, lg.grid, lg.rounds, 0ull, ~0ull,
           cl.team_bytes, cl.items_bytes, cl.staged ? nullptr : (double*)w.entries.p,
           cl.staged ? w.stage.p : nullptr, cl.staged ? (double*)w.wstage.p : nullptr,
-          cl.staged ? cl.cols_cap : 0, s, cl.staged ? 0 : 1);
+          cl.staged ? cl.cols_cap : 0, s, cl.staged ? 0 : 1, (unsigned long long*)w.counter.p);
       if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "grouped terms kernel");
       if (cl.staged) {
         e = launch_series_values(L.fp32, w.stage.p, (const double*)w.wstage.p, (lg.c1 - lg.c0) * cl.tpc, cl.cols_cap,

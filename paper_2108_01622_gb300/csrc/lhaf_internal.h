@@ -64,11 +64,14 @@ cudaError_t launch_terms(bool fp32, int team, const void* chat, const TermParams
 // + local index) and padding carry weight 0. With `stage`, chunk k's terms go to columns
 // (k - k_begin) * teams_per_cta + team; without, each team writes its double-double partial:
 // one per team over all its chunks, or (per_chunk) one per chunk and team at that column.
+// With next_chunk (a zeroed device counter) CTAs take chunks k_begin + atomicAdd(next_chunk, 1)
+// until k_end instead of the fixed grid-strided rounds.
 cudaError_t launch_grouped_terms(bool fp32, int team, const void* chat_pool, const BatchItem* jobs, int n_jobs,
                                  const long long* chunk_off, long long k_begin, long long k_end, int grid,
                                  int rounds, unsigned long long tb, unsigned long long te, int team_bytes,
                                  int items_bytes, double* partials, void* stage, double* wstage,
-                                 long long stage_ld, cudaStream_t stream, int per_chunk = 0);
+                                 long long stage_ld, cudaStream_t stream, int per_chunk = 0,
+                                 unsigned long long* next_chunk = nullptr);
 int grouped_ctas_per_sm(bool fp32, int team, size_t smem_bytes, bool staged);
 // Staged series of a grouped launch with each column's own degree and border (from its sieve):
 // weighted values (re, 0, im, 0) per column into values. h_max bounds the degrees.

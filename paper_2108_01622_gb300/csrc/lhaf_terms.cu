@@ -123,6 +123,28 @@ __device__ __forceinline__ void dd_add_dd(double& hi, double& lo, double bh, dou
   hi = t;
 }
 
+// acc += sum_{j0 <= j < j1} row[j] * col[j * ld]. Long sums keep two partial sums (even and odd
+// j) so that two independent multiply-add chains per component are in flight; short sums keep one
+// (merging costs two adds).
+template <typename V>
+__device__ __forceinline__ void dot_accumulate(V& acc, const V* row, const V* col, int ld, int j0, int j1) {
+  if (j1 - j0 >= 8) {
+    V b = cmake<V>(0, 0);
+    int j = j0;
+#pragma unroll 2
+    for (; j + 1 < j1; j += 2) {
+      cmac(acc, row[j], col[j * ld]);
+      cmac(b, row[j + 1], col[(j + 1) * ld]);
+    }
+    if (j < j1) cmac(acc, row[j], col[j * ld]);
+    acc.x += b.x;
+    acc.y += b.y;
+  } else {
+#pragma unroll 4
+    for (int j = j0; j < j1; j++) cmac(acc, row[j], col[j * ld]);
+  }
+}
+
 template <int G> __device__ __forceinline__ void team_sync() {
   if constexpr (G <= 32) {
     __syncwarp();
@@ -499,37 +521,45 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
       // multipliers l_i = K[i][k] / K[k+1][k], kept in column k below the subdiagonal
       for (int i = k + 2 + lt; i < nd; i += G) W[i * ld + k] = cmul(W[i * ld + k], ip);
       team_sync<G>();
-      // rows: K[i][j] -= l_i K[k+1][j] for i >= k+2, j >= k+1. Flattened over the team, two
-      // items per lane per pass (loads of both before either store), indices advanced without
-      // division.
+      // rows: K[i][j] -= l_i K[k+1][j] for i >= k+2, j >= k+1. Flattened over the team: passes of
+      // four items per lane while every lane has four (loads of all before any store), then one
+      // item per lane; indices advanced without division.
       const int cols = nd - k - 1;
       const int nrc = (cols - 1) * cols;
       {
         const int si = G / cols, sj = G - (G / cols) * cols;
         int ii = lt / cols, jj = lt - (lt / cols) * cols;
-        for (int w = lt; w < nrc; w += 2 * G) {
-          int ii2 = ii + si, jj2 = jj + sj;
-          if (jj2 >= cols) {
-            jj2 -= cols;
-            ii2++;
+        int w = 0;
+        for (; w + 4 * G <= nrc; w += 4 * G) {
+          V* pa[4];
+          V a[4], l[4], r[4];
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            pa[u] = W + (k + 2 + ii) * ld + (k + 1 + jj);
+            a[u] = *pa[u];
+            l[u] = W[(k + 2 + ii) * ld + k];
+            r[u] = W[(k + 1) * ld + k + 1 + jj];
+            ii += si;
+            jj += sj;
+            if (jj >= cols) {
+              jj -= cols;
+              ii++;
+            }
           }
-          const bool two = (w + G) < nrc;
-          V* p1 = W + (k + 2 + ii) * ld + (k + 1 + jj);
-          V* p2 = W + (k + 2 + ii2) * ld + (k + 1 + jj2);
-          V a1 = *p1;
-          const V l1 = W[(k + 2 + ii) * ld + k], r1 = W[(k + 1) * ld + k + 1 + jj];
-          V a2 = zero, l2 = zero, r2 = zero;
-          if (two) {
-            a2 = *p2;
-            l2 = W[(k + 2 + ii2) * ld + k];
-            r2 = W[(k + 1) * ld + k + 1 + jj2];
+#pragma unroll
+          for (int u = 0; u < 4; u++) cmsub(a[u], l[u], r[u]);
+#pragma unroll
+          for (int u = 0; u < 4; u++) *pa[u] = a[u];
+        }
+        for (; w < nrc; w += G) {
+          if (w + lt < nrc) {
+            V* p1 = W + (k + 2 + ii) * ld + (k + 1 + jj);
+            V a1 = *p1;
+            cmsub(a1, W[(k + 2 + ii) * ld + k], W[(k + 1) * ld + k + 1 + jj]);
+            *p1 = a1;
           }
-          cmsub(a1, l1, r1);
-          cmsub(a2, l2, r2);
-          *p1 = a1;
-          if (two) *p2 = a2;
-          ii = ii2 + si;
-          jj = jj2 + sj;
+          ii += si;
+          jj += sj;
           if (jj >= cols) {
             jj -= cols;
             ii++;
@@ -552,8 +582,7 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
             if (i < nd) {
               const int j0 = k + 2 + sgm * half;
               const int j1 = sgm ? nd : k + 2 + half;
-#pragma unroll 4
-              for (int j = j0; j < j1; j++) cmac(acc, W[i * ld + j], W[j * ld + k]);
+              dot_accumulate(acc, W + i * ld, W + k, ld, j0, j1);
             }
             acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
             acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
@@ -567,8 +596,7 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
         } else {
           for (int i = lt; i < nd; i += G) {
             V a = W[i * ld + k + 1];
-#pragma unroll 4
-            for (int j = k + 2; j < nd; j++) cmac(a, W[i * ld + j], W[j * ld + k]);
+            dot_accumulate(a, W + i * ld, W + k, ld, k + 2, nd);
             W[i * ld + k + 1] = a;
           }
         }
@@ -579,13 +607,25 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
     // ---- La Budde's recurrence, reverse (trailing blocks), truncated at degree Hl ----
     // q_j(t) = det(I - t K[j.., j..]) = (1 - t K_jj) q_{j+1} - sum_{l > j} c_{j,l} t^(l-j+1) q_{l+1}
     // with c_{j,l} = K_jl prod_{r=j+1..l} K_{r,r-1}, stored over K_jl (l - j <= Hl - 1).
-    for (int j = lt; j < nd - 1; j += G) {
-      V pi = one;
-      const int dmax = min(Hl - 1, nd - 1 - j);
-      for (int dp = 1; dp <= dmax; dp++) {
-        const int l = j + dp;
-        pi = cmul(pi, W[l * ld + l - 1]);
-        W[j * ld + l] = cmul(W[j * ld + l], pi);
+    // Each lane runs the product chains of up to four of its rows j side by side.
+    for (int j0 = lt; j0 < nd - 1; j0 += 4 * G) {
+      V pi[4];
+      int dm[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int j = j0 + u * G;
+        dm[u] = (j < nd - 1) ? min(Hl - 1, nd - 1 - j) : 0;
+        pi[u] = one;
+      }
+      for (int dp = 1; dp <= dm[0]; dp++) {
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          if (dp <= dm[u]) {
+            const int j = j0 + u * G, l = j + dp;
+            pi[u] = cmul(pi[u], W[l * ld + l - 1]);
+            W[j * ld + l] = cmul(W[j * ld + l], pi[u]);
+          }
+        }
       }
     }
     team_sync<G>();
@@ -607,53 +647,68 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
       const uint16_t* tab = by_d ? items + p.n_items : items;
       const int np = by_d ? npd : npe;
       const int nq = min(Hl, nd - l);
-      // Every item is dst <- a - b c: a push into acc_j, or the update of q_l[m]. Two items per
-      // lane per pass, loads first.
-      for (int w = lt; w < np + nq; w += 2 * G) {
-        V* dst[2];
-        V a[2], b[2], c[2];
-        bool ok[2];
+      // Every item is dst <- a - b c: a push into acc_j, or the update of q_l[m]; the items of one
+      // level are independent. Passes of four items per lane while every lane has four (loads
+      // first), then one item per lane.
+      auto load_item = [&](int x, V*& dst, V& a, V& b, V& c) -> bool {
+        if (x < np) {
+          // push q_{l+1} into the accumulator of q_j, j = l - d + 1
+          const int it = tab[x];
+          const int d = it >> 8, e = it & 255;
+          const int j = l - d + 1;
+          if (j >= 0 && e <= E) {
+            dst = W + (l + e) * ld + j;
+            a = *dst;
+            b = W[j * ld + l];
+            c = (e == 0) ? one : W[(l + e) * ld + l + 1];
+            return true;
+          }
+          return false;
+        }
+        // q_l[m] = q_{l+1}[m] - K_ll q_{l+1}[m-1] + acc_l[m]
+        const int m = x - np + 1;
+        dst = W + (l + m - 1) * ld + l;
+        V v = (m <= deg) ? W[(l + m) * ld + l + 1] : zero;
+        if (m >= 2) {
+          const V acc = *dst;
+          v.x += acc.x;
+          v.y += acc.y;
+        }
+        a = v;
+        b = hll;
+        c = (m == 1) ? one : ((m - 1 <= deg) ? W[(l + m - 1) * ld + l + 1] : zero);
+        return true;
+      };
+      const int nitems = np + nq;
+      int w = 0;
+      for (; w + 4 * G <= nitems; w += 4 * G) {
+        V* dst[4];
+        V a[4], b[4], c[4];
+        bool ok[4];
 #pragma unroll
-        for (int u = 0; u < 2; u++) {
-          const int x = w + u * G;
-          ok[u] = false;
+        for (int u = 0; u < 4; u++) {
           dst[u] = W;
           a[u] = zero;
           b[u] = zero;
           c[u] = zero;
-          if (x < np) {
-            // push q_{l+1} into the accumulator of q_j, j = l - d + 1
-            const int it = tab[x];
-            const int d = it >> 8, e = it & 255;
-            const int j = l - d + 1;
-            if (j >= 0 && e <= E) {
-              ok[u] = true;
-              dst[u] = W + (l + e) * ld + j;
-              a[u] = *dst[u];
-              b[u] = W[j * ld + l];
-              c[u] = (e == 0) ? one : W[(l + e) * ld + l + 1];
-            }
-          } else if (x < np + nq) {
-            // q_l[m] = q_{l+1}[m] - K_ll q_{l+1}[m-1] + acc_l[m]
-            const int m = x - np + 1;
-            ok[u] = true;
-            dst[u] = W + (l + m - 1) * ld + l;
-            V v = (m <= deg) ? W[(l + m) * ld + l + 1] : zero;
-            if (m >= 2) {
-              const V acc = *dst[u];
-              v.x += acc.x;
-              v.y += acc.y;
-            }
-            a[u] = v;
-            b[u] = hll;
-            c[u] = (m == 1) ? one : ((m - 1 <= deg) ? W[(l + m - 1) * ld + l + 1] : zero);
-          }
+          ok[u] = load_item(w + u * G + lt, dst[u], a[u], b[u], c[u]);
         }
 #pragma unroll
-        for (int u = 0; u < 2; u++) cmsub(a[u], b[u], c[u]);
+        for (int u = 0; u < 4; u++) cmsub(a[u], b[u], c[u]);
 #pragma unroll
-        for (int u = 0; u < 2; u++)
+        for (int u = 0; u < 4; u++)
           if (ok[u]) *dst[u] = a[u];
+      }
+      for (; w < nitems; w += G) {
+        const int x = w + lt;
+        if (x < nitems) {
+          V* dst = W;
+          V a = zero, b = zero, c = zero;
+          if (load_item(x, dst, a, b, c)) {
+            cmsub(a, b, c);
+            *dst = a;
+          }
+        }
       }
       V hnext = zero;
       if (l > 0) hnext = W[(l - 1) * ld + l - 1];
@@ -815,13 +870,15 @@ grouped_terms_kernel(const typename Cx<R>::t* __restrict__ chat_pool, const Batc
                      const long long* __restrict__ chunk_off, long long k_begin, long long k_end, int rounds,
                      unsigned long long tb, unsigned long long te, int team_bytes, int items_bytes,
                      double* __restrict__ partials, typename Cx<R>::t* __restrict__ stage,
-                     double* __restrict__ wstage, long long stage_ld, int per_chunk) {
+                     double* __restrict__ wstage, long long stage_ld, int per_chunk,
+                     unsigned long long* __restrict__ next_chunk) {
   using V = typename Cx<R>::t;
   constexpr int CTA = cta_of(G);
   constexpr int TEAMS = CTA / G;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TermParams sp;
   __shared__ int s_job, s_Hl;
+  __shared__ long long s_k;
   const int team = threadIdx.x / G;
   const int lt = threadIdx.x - team * G;
   if (threadIdx.x == 0) {
@@ -829,8 +886,19 @@ grouped_terms_kernel(const typename Cx<R>::t* __restrict__ chat_pool, const Batc
     s_Hl = -1;
   }
   double rh = 0.0, rl = 0.0, ih = 0.0, il = 0.0;
-  for (int r = 0; r < rounds; r++) {
-    const long long k = k_begin + blockIdx.x + (long long)r * gridDim.x;
+  for (int r = 0;; r++) {
+    // chunk of this round: taken from the shared counter (CTAs whose SM sub-partitions share a
+    // less loaded FP64 unit take more chunks), or grid-strided without one
+    long long k;
+    if (next_chunk) {
+      __syncthreads();  // the previous s_k has been read by every thread
+      if (threadIdx.x == 0) s_k = k_begin + (long long)atomicAdd(next_chunk, 1ull);
+      __syncthreads();
+      k = s_k;
+    } else {
+      if (r >= rounds) break;
+      k = k_begin + blockIdx.x + (long long)r * gridDim.x;
+    }
     if (k >= k_end) break;  // uniform over the CTA
     // sieve of chunk k: the last j with chunk_off[j] <= k
     int lo = 0, hi = n_jobs - 1;
@@ -1527,7 +1595,8 @@ cudaError_t launch_grouped_terms(bool fp32, int team, const void* chat_pool, con
                                  const long long* chunk_off, long long k_begin, long long k_end, int grid,
                                  int rounds, unsigned long long tb, unsigned long long te, int team_bytes,
                                  int items_bytes, double* partials, void* stage, double* wstage,
-                                 long long stage_ld, cudaStream_t stream, int per_chunk) {
+                                 long long stage_ld, cudaStream_t stream, int per_chunk,
+                                 unsigned long long* next_chunk) {
   const bool staged = stage != nullptr;
   const void* k = pick_grouped(fp32, team, staged);
   if (!k || grid <= 0 || n_jobs <= 0) return cudaErrorInvalidValue;
@@ -1537,7 +1606,8 @@ cudaError_t launch_grouped_terms(bool fp32, int team, const void* chat_pool, con
   void* args[] = {(void*)&chat_pool, (void*)&jobs,       (void*)&n_jobs,    (void*)&chunk_off,
                   (void*)&k_begin,   (void*)&k_end,      (void*)&rounds,    (void*)&tb,
                   (void*)&te,        (void*)&team_bytes, (void*)&items_bytes, (void*)&partials,
-                  (void*)&stage,     (void*)&wstage,     (void*)&stage_ld, (void*)&per_chunk};
+                  (void*)&stage,     (void*)&wstage,     (void*)&stage_ld, (void*)&per_chunk,
+                  (void*)&next_chunk};
   return cudaLaunchKernel(k, dim3(grid), dim3(cta_of(team)), args, smem, stream);
 }
 
