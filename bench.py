@@ -31,6 +31,9 @@ UNIT = "terms/s"
 WORKLOAD = ("collision-pattern loop hafnian: 100-mode Haar interferometer, r ~ U[1.0,1.6], gamma = 0, "
             "40 photons over 22 modes with counts 1..4 (seeded multinomial), complex128, repeated-pair sieve")
 KERNEL_NAME = "grouped_terms_kernel (FP64 sieve terms of the zero-digit groups)"
+# DRAM bytes (read + write) of one grouped_terms_kernel launch on this workload, from the ncu
+# capture summarised in profiles/grouped_terms_kernel_collision40.md (None once the kernel changes)
+KERNEL_TRAFFIC_BYTES = 187904
 NOMINAL_FP64_GFLOPS = 152 * 4 * 0.5 * 2 * 2.070  # SMs x sub-partitions x FMA lanes/clk x 2 flops x GHz
 
 
@@ -275,7 +278,8 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": KERNEL_NAME if groups else "terms_kernel (FP64 sieve terms)",
                      "achieved": achieved, "peak": NOMINAL_FP64_GFLOPS / 1e3, "unit": "TFLOP/s",
-                     "frac": achieved / (NOMINAL_FP64_GFLOPS / 1e3), "traffic": None,
+                     "frac": achieved / (NOMINAL_FP64_GFLOPS / 1e3),
+                     "traffic": KERNEL_TRAFFIC_BYTES if groups else None,
                      "peak_source": "derived: 152 SMs x 4 sub-partitions x 0.5 FP64 FMA lanes/clk x 2 x 2.070 GHz",
                      "fp64_probe_tflops": fp64_gflops / 1e3,
                      "frac_of_probe": achieved / (fp64_gflops / 1e3),
