@@ -74,23 +74,46 @@ __device__ __forceinline__ unsigned long long mag_key(float2 z) {
   return a > b ? a : b;
 }
 
-// 1 / z. The exponent of max(|re|, |im|) is scaled out first (exact power-of-two scaling), so
-// d = |z s|^2 lies in [1, 8). 1/d: FP32 reciprocal seed refined by two Newton-Raphson steps
-// r <- r (2 - d r) (relative error ~2^-23 -> ~2^-46 -> below 2^-53). Returns 0 for z == 0.
+// x * 2^k by exponent arithmetic (integer instructions, no FP64 issue slot): exact for normal x
+// and normal results; zero and subnormal x, and results below the normal range, give a signed
+// zero; results above it give a signed infinity.
+__device__ __forceinline__ double scale2(double x, int k) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  const int ne = ex + k;
+  const long long sign = b & (long long)0x8000000000000000ull;
+  if (ex == 0 || ne <= 0) return __longlong_as_double(sign);
+  if (ne >= 2047) return __longlong_as_double(sign | (long long)0x7ff0000000000000ull);
+  return __longlong_as_double((b & ~(long long)0x7ff0000000000000ull) | ((long long)ne << 52));
+}
+
+// 1 / z = conj(z) / |z|^2. The exponent of max(|re|, |im|) is scaled out first (by exponent
+// arithmetic), so d = |z s|^2 lies in [1, 8). 1/d: an FP32 reciprocal of d's leading bits (moved
+// between the formats with integer instructions) refined by two Newton-Raphson steps
+// r <- r (2 - d r) (relative error ~2^-23 -> ~2^-46 -> below 2^-53); the result is scaled back the
+// same way. Returns 0 for z == 0.
 __device__ __forceinline__ double2 crecip(double2 z) {
   const unsigned long long k = mag_key(z);
   if (k == 0ull) return make_double2(0.0, 0.0);
   int e = (int)(k >> 52);  // biased exponent of the larger part (0 for subnormals)
   if (e < 1) e = 1;
   if (e > 2045) e = 2045;
-  const double sc = __longlong_as_double((long long)(2046 - e) << 52);  // 2^(1023 - (e - 1023))
-  const double xs = z.x * sc, ys = z.y * sc;
+  const int sh = 1023 - e;  // s = 2^sh brings the larger part into [1, 2)
+  const double xs = scale2(z.x, sh), ys = scale2(z.y, sh);
   const double d = fma(xs, xs, ys * ys);
-  double r = (double)__frcp_rn((float)d);
+  // float with d's exponent and its 23 leading mantissa bits (d in [1, 8): exponent 0..2)
+  const long long db = __double_as_longlong(d);
+  if (db == 0) return make_double2(0.0, 0.0);  // both parts subnormal: treated as a zero pivot
+  const int de = (int)((db >> 52) & 0x7ff) - 1023;
+  const unsigned fm = (unsigned)((db >> 29) & 0x7fffff);
+  const float rf = __frcp_rn(__int_as_float(((de + 127) << 23) | (int)fm));
+  const int fb = __float_as_int(rf);
+  double r = __longlong_as_double(((long long)(((fb >> 23) & 0xff) - 127 + 1023) << 52) |
+                                  ((long long)(fb & 0x7fffff) << 29));
   r = fma(r, fma(-d, r, 1.0), r);
   r = fma(r, fma(-d, r, 1.0), r);
-  const double rs = r * sc;
-  return make_double2(xs * rs, flip(ys) * rs);
+  // 1/z = (xs, -ys) * r * s
+  return make_double2(scale2(xs * r, sh), scale2(flip(ys) * r, sh));
 }
 __device__ __forceinline__ float2 crecip(float2 z) {
   const unsigned k = (unsigned)mag_key(z);
@@ -123,25 +146,31 @@ __device__ __forceinline__ void dd_add_dd(double& hi, double& lo, double bh, dou
   hi = t;
 }
 
-// acc += sum_{j0 <= j < j1} row[j] * col[j * ld]. Long sums keep two partial sums (even and odd
-// j) so that two independent multiply-add chains per component are in flight; short sums keep one
-// (merging costs two adds).
+// acc += sum_{j0 <= j < j1} row[j] * col[j * ld], with running pointers. Long sums keep two
+// partial sums (even and odd j) so that two independent multiply-add chains per component are in
+// flight; short sums keep one (merging costs two adds).
 template <typename V>
 __device__ __forceinline__ void dot_accumulate(V& acc, const V* row, const V* col, int ld, int j0, int j1) {
-  if (j1 - j0 >= 8) {
+  const V* pr = row + j0;
+  const V* pc = col + j0 * ld;
+  int n = j1 - j0;
+  if (n >= 8) {
     V b = cmake<V>(0, 0);
-    int j = j0;
-#pragma unroll 2
-    for (; j + 1 < j1; j += 2) {
-      cmac(acc, row[j], col[j * ld]);
-      cmac(b, row[j + 1], col[(j + 1) * ld]);
+    for (; n >= 2; n -= 2) {
+      cmac(acc, pr[0], pc[0]);
+      cmac(b, pr[1], pc[ld]);
+      pr += 2;
+      pc += 2 * ld;
     }
-    if (j < j1) cmac(acc, row[j], col[j * ld]);
+    if (n) cmac(acc, pr[0], pc[0]);
     acc.x += b.x;
     acc.y += b.y;
   } else {
-#pragma unroll 4
-    for (int j = j0; j < j1; j++) cmac(acc, row[j], col[j * ld]);
+    for (; n > 0; n--) {
+      cmac(acc, *pr, *pc);
+      pr++;
+      pc += ld;
+    }
   }
 }
 
@@ -177,6 +206,7 @@ struct TeamScratch {  // small per-team area
   double pvx[4], pvy[4];
   double weight;
   int delta[kMaxPairs];
+  double fdelta[kMaxPairs];  // delta as a double (converted once per pair and term)
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -411,6 +441,7 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
         wq *= binom_d(eta, k);
         par ^= (k & 1);
         ts->delta[q] = eta - 2 * k;
+        ts->fdelta[q] = (double)(eta - 2 * k);
         if (q == p.hp && !(p.hp_even && 2 * k == eta)) wq *= 2.0;  // sign-symmetry halving
       }
 #pragma unroll
@@ -423,9 +454,11 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
     team_sync<G>();
 
     // ---- working matrix K[i][j] = Chat[i][partner(j)] * delta_hat(j) ----
+    // Column by column, so that the lanes of a team mostly share one column's factor and the FP64
+    // multiplies issue only for columns whose |delta'| > 1 in some team of the warp.
     {
-      const int si = G / nd, sj = G - (G / nd) * nd;
-      int i = lt / nd, j = lt - (lt / nd) * nd;
+      const int sj = G / nd, si = G - (G / nd) * nd;
+      int j = lt / nd, i = lt - (lt / nd) * nd;
       for (int w = lt; w < nd * nd; w += G) {
         int jj = j, dl = 1;
         if (j >= bord) {
@@ -438,16 +471,16 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
           c.x = flip(c.x);
           c.y = flip(c.y);
         } else if (dl != 1) {
-          const R f = (R)dl;
+          const R f = (R)ts->fdelta[(j - bord) >> 1];
           c.x *= f;
           c.y *= f;
         }
         W[i * ld + j] = c;
-        i += si;
         j += sj;
-        if (j >= nd) {
-          j -= nd;
-          i++;
+        i += si;
+        if (i >= nd) {
+          i -= nd;
+          j++;
         }
       }
     }
