@@ -388,6 +388,30 @@ def run_extras(ctx, torch, dev, lg, wl):
     out["batched_small"] = {"workload": "2048 loop hafnians, N~U{8..16}, same state family",
                             "batched_ms": tbs, "graph_replay_ms": tgs, "plain_ms": tps,
                             "batched_over_plain_speedup": tps / tbs, "graph_over_plain_speedup": tps / tgs}
+    # batched mode of one chain-rule step (App. B.5): the next mode's outcomes n = 0..8 at once,
+    # against the same nine loop hafnians as one batch
+    cb = wl.chain_rule_batch(seed=11, count=64, n_lo=26, n_hi=30)
+    ci = max(range(len(cb.reps)), key=lambda i: int(np.sum(cb.reps[i])))
+    fixed = np.array(cb.reps[ci], dtype=np.int32)
+    mode = int(np.nonzero(fixed == 0)[0][0])
+    gm = np.array(cb.gammas[ci])
+    n_cut = 8
+    pats = np.repeat(fixed[None, :], n_cut + 1, axis=0)
+    pats[:, mode] = np.arange(n_cut + 1)
+    gms = np.repeat(gm[None, :], n_cut + 1, axis=0)
+    ctx.lhaf_batched_mode(cb.B, gm, fixed, mode, n_cut)
+    ctx.lhaf_batched(cb.B, gms, pats)
+    tm = _timed(torch, lambda: ctx.lhaf_batched_mode(cb.B, gm, fixed, mode, n_cut), reps=3)
+    tbp = _timed(torch, lambda: ctx.lhaf_batched(cb.B, gms, pats), reps=3)
+    ctx.lhaf(cb.B, gm, pats[-1])
+    tl = _timed(torch, lambda: ctx.lhaf(cb.B, gm, pats[-1]), reps=3)
+    vm = ctx.lhaf_batched_mode(cb.B, gm, fixed, mode, n_cut)
+    vb, _ = ctx.lhaf_batched(cb.B, gms, pats)
+    out["batched_mode"] = {"workload": f"chain-rule step: {int(fixed.sum())} fixed photons, outcomes 0..{n_cut} "
+                                       "of the next mode, 50-mode lossy state",
+                           "batched_mode_ms": tm, "batched_patterns_ms": tbp, "speedup": tbp / tm,
+                           "largest_outcome_alone_ms": tl, "batched_mode_over_largest": tm / tl,
+                           "max_rel_diff": float(np.max(np.abs(vm - vb) / np.abs(vb)))}
     # adjoint: one 32-photon outcome of a 40-mode state
     gb = wl.gradient_batch(seed=4, count=2)
     import time as _t

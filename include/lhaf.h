@@ -180,6 +180,19 @@ lhaf_status lhaf_batched_plan_exec(lhaf_batch_plan* plan, const lhaf_c128* B, co
                                    lhaf_c128* out, lhaf_status* item_status, lhaf_stats* stats);
 void lhaf_batched_plan_destroy(lhaf_batch_plan* plan);
 
+/* Batched mode of one chain-rule step (App. A.2; App. B.5): out[n] = lhaf(B_{reps + n e_mode}) for
+ * n = 0..n_cut, where the batched mode has reps[mode] == 0. The fixed photons are paired greedily,
+ * the batched mode's photons with themselves (floor(n/2) repeats) and an odd n's last one with the
+ * fixed leftover photon or a pad index; per outcome parity one sieve runs over the fixed digits and
+ * the self pair's delta' in -A..A (A = floor(n_max/2)), so each term's Hessenberg reduction and
+ * characteristic polynomial serve every outcome (its series gives all degrees up to the largest).
+ *   B, gamma, reps: HOST, as for lhaf() (gamma NULL: loops from diag(B)); out: HOST, n_cut + 1.
+ *   flags: LHAF_PLAIN_ACCUM only. Errors: LHAF_EINVAL for bad arguments or reps[mode] != 0;
+ *   LHAF_ETOOBIG when ceil((N_fixed + n_cut)/2) exceeds 24 (the staged series limit) or the
+ *   working dimension exceeds LHAF_MAX_DIM. Synchronous. */
+lhaf_status lhaf_batched_mode(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128* gamma, const int32_t* reps,
+                              int mode, int n_cut, uint32_t flags, lhaf_c128* out, lhaf_stats* stats);
+
 /* Value and gradient of lhaf(B_n) (the paper has no gradient; it follows from the definition, App.
  * B: the derivative of a matching sum with respect to one weight is the matching sum over the
  * remaining indices, e.g. d lhaf / d gamma_m = n_m lhaf(n - e_m)). Computed by a per-term adjoint

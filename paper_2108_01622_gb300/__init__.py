@@ -94,6 +94,9 @@ def _lib():
         L.lhaf_batched_plan_exec.restype = c.c_int
         L.lhaf_batched_plan_destroy.argtypes = [vp]
         L.lhaf_batched_plan_destroy.restype = None
+        L.lhaf_batched_mode.argtypes = [vp, c.c_int, vp, vp, vp, c.c_int, c.c_int, c.c_uint32, vp,
+                                        ctypes.POINTER(Stats)]
+        L.lhaf_batched_mode.restype = c.c_int
         L.lhaf_fp64_probe.argtypes = [c.c_int, ctypes.POINTER(c.c_double)]
         L.lhaf_fp64_probe.restype = c.c_int
         _LIB = L
@@ -307,6 +310,20 @@ class Context:
         """A BatchedPlan for the patterns `reps` (batch x M): planned, tuned on (B, gammas) and
         captured in a CUDA graph once; BatchedPlan.run evaluates new values of B and gammas."""
         return BatchedPlan(self, B, gammas, reps, flags)
+
+    def lhaf_batched_mode(self, B, gamma, reps, mode: int, n_cut: int, flags: int = 0, stats: bool = False):
+        """lhaf(B_{reps + n e_mode}) for n = 0..n_cut (reps[mode] == 0) with shared sieve terms
+        (App. B.5). Host inputs; returns a complex128 array of n_cut + 1 values."""
+        Bh = _host_c128(B)
+        M = Bh.shape[0]
+        gh = None if gamma is None else _host_c128(gamma)
+        r = _reps_arr(reps, M)
+        out = np.zeros(n_cut + 1, np.complex128)
+        st = Stats()
+        _check(self._lib.lhaf_batched_mode(self._h, M, Bh.ctypes.data, None if gh is None else gh.ctypes.data,
+                                           r.ctypes.data, mode, n_cut, flags, out.ctypes.data,
+                                           ctypes.byref(st) if stats else None), "lhaf_batched_mode")
+        return (out, st.as_dict()) if stats else out
 
     def gbs_pattern_prob(self, U, r, alpha, n, flags: int = 0):
         """(P(n), lhaf(B_n)) for the pure state (U, r, alpha) (App. A, Eq. mixed_prob)."""

@@ -183,6 +183,8 @@ void fill_params(const Plan& pl, bool fp32, bool staged, int team, uint32_t flag
   for (int q = 0; q < pl.P && q < (int)pl.skip.size(); q++)
     if (pl.skip[q]) p.skip_mask |= 1u << q;
   p.wscale = pl.wscale;
+  p.bq = -1;  // no batched-mode self pair
+  p.bA = 0;
   p.n_items = pl.Hl * (pl.Hl - 1) / 2;
   p.team_bytes = (int)team_shared_bytes(fp32, pl.nd, pl.H, pl.P, staged);
   p.items_bytes = (int)(cta_shared_bytes(fp32, team, pl.nd, pl.H, pl.Hl, pl.P, staged) -

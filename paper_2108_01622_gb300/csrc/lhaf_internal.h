@@ -34,7 +34,9 @@ struct TermParams {
   unsigned long long total_teams;
   unsigned long long t_lo;            // terms below t_lo are outside the range (weight 0)
   int stage_pad;                      // 1: stage out-of-range terms too, with weight 0
-  int pad_;
+  int bq;                             // batched-mode self pair (its digit k gives delta' = bA - k), or -1
+  int bA;                             // largest self-pair repeat of the batched mode
+  int pad2_;
 };
 
 // One sieve of a grouped launch: a loop hafnian's whole sieve or one of its zero-digit groups.
@@ -78,6 +80,12 @@ int grouped_ctas_per_sm(bool fp32, int team, size_t smem_bytes, bool staged);
 cudaError_t launch_series_values(bool fp32, const void* stage, const double* wstage, long long count,
                                  long long stage_ld, const BatchItem* jobs, int n_jobs, const long long* chunk_off,
                                  long long k_begin, int tpc, int h_max, double* values, cudaStream_t stream);
+// Batched mode (App. B.5): series of count staged terms to degree h_max, then per outcome t the
+// weight coef[t * (2A + 1) + delta_self + A] (delta_self staged in wstage[stage_ld + term]) times
+// e_{h_out[t]}, summed per 64-term block into partials[4 * (t * blocks + block)].
+cudaError_t launch_series_modes(bool fp32, const void* stage, const double* wstage, long long count,
+                                long long stage_ld, int h_max, int bord, int n_out, const int* h_out,
+                                const double* coef, int A, double* partials, cudaStream_t stream);
 // acc[4 * seg_item[s]] += double-double sum of entries seg_begin[s] .. seg_begin[s+1]-1.
 cudaError_t launch_segment_reduce(const double* entries, const long long* seg_begin, const int* seg_item, int n_seg,
                                   int plain, double* acc, cudaStream_t stream);

@@ -140,6 +140,8 @@ extern "C" lhaf_status lhaf_noalloc(int device, void* cuda_stream, int M, const 
   p.plain = (flags & LHAF_PLAIN_ACCUM) ? 1 : 0;
   p.skip_mask = 0u;
   p.wscale = 1.0;
+  p.bq = -1;
+  p.bA = 0;
   p.n_items = pl.Hl * (pl.Hl - 1) / 2;
   p.team_bytes = (int)team_shared_bytes(fp32, pl.nd, pl.H, pl.P);
   p.items_bytes =

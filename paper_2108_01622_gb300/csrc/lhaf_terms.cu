@@ -207,6 +207,8 @@ struct TeamScratch {  // small per-team area
   double weight;
   int delta[kMaxPairs];
   double fdelta[kMaxPairs];  // delta as a double (converted once per pair and term)
+  int dself;                 // batched-mode self-pair delta' of the term
+  int pad_;
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -437,6 +439,16 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
         }
         const int eta = p.eta[q];
         int k = (int)(qt % rad);
+        if (q == p.bq) {
+          // batched-mode self pair: delta' runs over bA, bA - 1, ..., -bA (or bA..0 when this is
+          // the halved digit); its binomial weight depends on the outcome and is applied later
+          const int dlt = p.bA - k;
+          ts->delta[q] = dlt;
+          ts->fdelta[q] = (double)dlt;
+          ts->dself = dlt;
+          if (q == p.hp && dlt != 0) wq *= 2.0;
+          continue;
+        }
         if (((p.skip_mask >> q) & 1u) && 2 * k >= eta) k++;  // zero-digit group: no middle digit
         wq *= binom_d(eta, k);
         par ^= (k & 1);
@@ -767,7 +779,10 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
           }
           stage[(long long)x * stage_ld + col] = (x < h) ? am : cmake<V>(am.x - bm.x, am.y - bm.y);
         }
-        if (lt == 0) wstage[col] = ts->weight;
+        if (lt == 0) {
+          wstage[col] = ts->weight;
+          if (p.bq >= 0) wstage[stage_ld + col] = (double)ts->dself;  // second row: the self delta'
+        }
       }
       team_sync<G>();
     } else {
@@ -1416,6 +1431,100 @@ series_values_kernel(const typename Cx<R>::t* __restrict__ stage, const double* 
   o[3] = 0.0;
 }
 
+// Batched mode (App. B.5): the staged terms of one parity class, one term per thread. The series
+// runs to the class's largest degree h_max; outcome t (degree h_t) takes e_{h_t} with the weight
+// coef[t][delta_self + A] (the self pair's binomial and sign for that outcome, 0 where the term
+// does not occur). Per block and outcome the double-double sum goes to
+// partials[4 * (t * gridDim.x + block)].
+template <typename R>
+__global__ void __launch_bounds__(kSeriesThreads)
+series_modes_kernel(const typename Cx<R>::t* __restrict__ stage, const double* __restrict__ wstage, long long count,
+                    long long stage_ld, int h_max, int bord, int n_out, const int* __restrict__ h_out,
+                    const double* __restrict__ coef, int A, double* __restrict__ partials) {
+  using V = typename Cx<R>::t;
+  extern __shared__ __align__(16) unsigned char smem[];
+  V* SR = reinterpret_cast<V*>(smem);                 // (h_max + 2) x threads
+  V* Sp = SR + (size_t)(h_max + 2) * kSeriesThreads;  // (h_max + 1) x threads
+  V* Sz = Sp + (size_t)(h_max + 1) * kSeriesThreads;
+  V* Se = Sz + (size_t)(h_max + 1) * kSeriesThreads;
+  __shared__ double red[4][kSeriesThreads];
+  const int tid = threadIdx.x;
+  const long long tt = (long long)blockIdx.x * kSeriesThreads + tid;
+  const V zero = cmake<V>((R)0, (R)0);
+  const bool live = tt < count;
+  double w = 0.0;
+  int ds = 0;
+#define SIDX(i) ((size_t)(i) * kSeriesThreads + tid)
+  if (live) {
+    const int h = h_max;
+    auto A_ = [&](int m) -> V { return stage[(long long)(m - 1) * stage_ld + tt]; };
+    auto C_ = [&](int m) -> V { return bord ? stage[(long long)(h + m - 1) * stage_ld + tt] : zero; };
+    SR[SIDX(0)] = zero;
+    SR[SIDX(1)] = C_(1);
+    Se[SIDX(0)] = cmake<V>((R)1, (R)0);
+    for (int k = 1; k <= h; k++) {
+      V sR = zero, sp = zero;
+      for (int i = 1; i <= k; i++) {
+        const V ai = A_(i);
+        if (bord) cmac(sR, ai, SR[SIDX(k + 1 - i)]);
+        if (i < k) cmac(sp, ai, Sp[SIDX(k - i)]);
+      }
+      const V ck = C_(k + 1), ak = A_(k);
+      const R kk = (R)k;
+      const V Rk = cmake<V>(ck.x - sR.x, ck.y - sR.y);
+      const V pk = cmake<V>(-rfma(kk, ak.x, sp.x), -rfma(kk, ak.y, sp.y));
+      const V zk = cmake<V>((R)0.5 * rfma(kk, Rk.x, pk.x), (R)0.5 * rfma(kk, Rk.y, pk.y));
+      SR[SIDX(k + 1)] = Rk;
+      Sp[SIDX(k)] = pk;
+      Sz[SIDX(k)] = zk;
+      V se = zero;
+      for (int j = 1; j <= k; j++) cmac(se, Sz[SIDX(j)], Se[SIDX(k - j)]);
+      const R ik = (R)1 / kk;
+      Se[SIDX(k)] = cmake<V>(se.x * ik, se.y * ik);
+    }
+    w = wstage[tt];
+    ds = A > 0 ? (int)wstage[stage_ld + tt] : 0;  // without a self pair every delta' is 0
+  }
+  for (int t = 0; t < n_out; t++) {
+    double fr = 0.0, fi = 0.0;
+    if (live && ds >= -A && ds <= A) {
+      const double c = coef[(size_t)t * (2 * A + 1) + (ds + A)];
+      const int ht = h_out[t];
+      if (c != 0.0 && ht >= 0 && ht <= h_max) {
+        const V f = Se[SIDX(ht)];
+        fr = (double)f.x * w * c;
+        fi = (double)f.y * w * c;
+      }
+    }
+    red[0][tid] = fr;
+    red[1][tid] = 0.0;
+    red[2][tid] = fi;
+    red[3][tid] = 0.0;
+    __syncthreads();
+    for (int off = kSeriesThreads / 2; off >= 1; off >>= 1) {
+      if (tid < off) {
+        double a = red[0][tid], b = red[1][tid], cc = red[2][tid], d = red[3][tid];
+        dd_add_dd(a, b, red[0][tid + off], red[1][tid + off]);
+        dd_add_dd(cc, d, red[2][tid + off], red[3][tid + off]);
+        red[0][tid] = a;
+        red[1][tid] = b;
+        red[2][tid] = cc;
+        red[3][tid] = d;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      double* o = partials + 4ll * ((long long)t * gridDim.x + blockIdx.x);
+      o[0] = red[0][0];
+      o[1] = red[1][0];
+      o[2] = red[2][0];
+      o[3] = red[3][0];
+    }
+    __syncthreads();
+  }
+#undef SIDX
+}
+
 // Per segment s: double-double sum of entries seg_begin[s] .. seg_begin[s+1]-1 (4 doubles each),
 // added to acc[4 * seg_item[s]] (one warp per segment; segments of one launch name distinct items).
 __global__ void __launch_bounds__(128)
@@ -1501,6 +1610,20 @@ cudaError_t launch_series_values(bool fp32, const void* stage, const double* wst
   void* args[] = {(void*)&stage,    (void*)&wstage,  (void*)&count, (void*)&stage_ld,
                   (void*)&jobs,     (void*)&n_jobs,  (void*)&chunk_off, (void*)&k_begin,
                   (void*)&tpc,      (void*)&h_max,   (void*)&values};
+  return cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(kSeriesThreads), args, smem, stream);
+}
+
+cudaError_t launch_series_modes(bool fp32, const void* stage, const double* wstage, long long count,
+                                long long stage_ld, int h_max, int bord, int n_out, const int* h_out,
+                                const double* coef, int A, double* partials, cudaStream_t stream) {
+  if (count <= 0) return cudaSuccess;
+  const size_t smem = series_shared_bytes(fp32, h_max);
+  const void* k = fp32 ? (const void*)series_modes_kernel<float> : (const void*)series_modes_kernel<double>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long blocks = series_blocks(count);
+  void* args[] = {(void*)&stage,  (void*)&wstage, (void*)&count, (void*)&stage_ld, (void*)&h_max, (void*)&bord,
+                  (void*)&n_out,  (void*)&h_out,  (void*)&coef,  (void*)&A,        (void*)&partials};
   return cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(kSeriesThreads), args, smem, stream);
 }
 

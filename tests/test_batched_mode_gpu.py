@@ -1,0 +1,96 @@
+"""GPU parity of the batched mode of one chain-rule step (App. A.2, App. B.5): every outcome
+n = 0..n_cut of the batched mode against the oracle's own loop hafnian of that pattern (its own
+greedy pairing), and against one lhaf call per outcome."""
+import numpy as np
+import pytest
+
+from oracle import lhaf_oracle as lo
+from paper_2108_01622_gb300 import workloads as wl
+from tests.libutil import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def lg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return ensure_built()
+
+
+@pytest.fixture(scope="module")
+def ctx(lg):
+    c = lg.Context(0)
+    yield c
+    c.close()
+
+
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+def _check(ctx, B, gamma, reps, mode, n_cut):
+    out = ctx.lhaf_batched_mode(B, gamma, reps, mode, n_cut)
+    assert out.shape == (n_cut + 1,)
+    g = np.diag(B).copy() if gamma is None else gamma
+    for n in range(n_cut + 1):
+        r = np.array(reps, dtype=np.int64).copy()
+        r[mode] = n
+        ref = lo.lhaf_repeated(B, g, r)
+        if abs(ref) < 1e-12:
+            assert abs(out[n]) < 1e-11, (reps, mode, n, out[n], ref)
+        else:
+            assert rel(out[n], ref) < TOL, (reps, mode, n, out[n], ref)
+    return out
+
+
+@pytest.mark.parametrize("reps,mode,n_cut", [
+    ((1, 1, 0, 2), 2, 6),       # N_fixed even, a repeated fixed pair
+    ((1, 2, 0, 2), 2, 7),       # N_fixed odd: the odd outcomes pair the leftover with the mode
+    ((0, 0, 0, 0), 1, 6),       # nothing fixed: the single-mode loop hafnians
+    ((2, 0, 2, 0), 1, 5),       # only even fixed pairs
+    ((3, 1, 1, 0, 1), 3, 8),
+])
+@pytest.mark.parametrize("loops", [True, False])
+def test_batched_mode_small_vs_oracle(ctx, reps, mode, n_cut, loops):
+    p = wl.small_problem(seed=sum(reps) + 7 * mode + n_cut, M=len(reps), reps=reps, loops=loops)
+    _check(ctx, p.B, p.gamma, list(reps), mode, n_cut)
+
+
+def test_batched_mode_gamma_none_and_n_cut_zero(ctx):
+    p = wl.small_problem(seed=3, M=5, reps=(1, 1, 1, 0, 1), loops=True)
+    _check(ctx, p.B, None, [1, 1, 1, 0, 1], 3, 4)
+    out = ctx.lhaf_batched_mode(p.B, p.gamma, [1, 1, 1, 0, 1], 3, 0)
+    assert rel(out[0], lo.lhaf_repeated(p.B, p.gamma, [1, 1, 1, 0, 1])) < TOL
+
+
+def test_batched_mode_chain_rule_step_matches_single_calls(ctx, lg):
+    # a chain-rule step on the lossy 50-mode state: 20 photons fixed, the next mode batched to 8
+    b = wl.chain_rule_batch(seed=5, count=8)
+    reps = np.array(b.reps[0], dtype=np.int32)
+    gamma = np.array(b.gammas[0])
+    mode = int(np.nonzero(reps == 0)[0][0])
+    n_cut = 8
+    out, st = ctx.lhaf_batched_mode(b.B, gamma, reps, mode, n_cut, stats=True)
+    singles = []
+    for n in range(n_cut + 1):
+        r = reps.copy()
+        r[mode] = n
+        singles.append(ctx.lhaf(b.B, gamma, r))
+        # two different exact sieves (the batched mode pairs the mode with itself, the single call
+        # pairs greedily), each within TOL of the value on these cancelling items
+        assert rel(out[n], singles[-1]) < 2 * TOL, (n, out[n], singles[-1])
+    assert st["terms"] > 0 and st["launches"] >= 4
+
+
+def test_batched_mode_rejects_bad_arguments(ctx, lg):
+    p = wl.small_problem(seed=4, M=3, reps=(1, 1, 1), loops=True)
+    with pytest.raises(lg.LhafError) as e:
+        ctx.lhaf_batched_mode(p.B, p.gamma, [1, 1, 1], 1, 3)  # the batched mode must be empty
+    assert e.value.status == 1
+    with pytest.raises(lg.LhafError) as e:
+        ctx.lhaf_batched_mode(p.B, p.gamma, [20, 20, 0], 2, 12)  # degree 26 > 24
+    assert e.value.status == 2
