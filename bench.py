@@ -318,7 +318,8 @@ def _timed(torch, fn, reps=3):
 def run_extras(ctx, torch, dev, lg, wl):
     """The rest of the metric, each on its own workload (untimed by the step loop above):
     ms per 60-photon loop hafnian (projected from a timed slice of its sieve terms), the FP32-term
-    variant on the same slice, batched vs one call per item on a chain-rule batch, and the adjoint."""
+    variant on the same slice, batched vs one call per item on a chain-rule batch, the batched mode of
+    one chain-rule step, a mixed-state probability, and the adjoint."""
     out = {}
     # 60-photon collision-free lhaf (100-mode Haar, r ~ U[1.2, 1.8]): 2^29 terms of dimension 61
     p60 = wl.large_lhaf_60(seed=5)
@@ -412,6 +413,15 @@ def run_extras(ctx, torch, dev, lg, wl):
                            "batched_mode_ms": tm, "batched_patterns_ms": tbp, "speedup": tbp / tm,
                            "largest_outcome_alone_ms": tl, "batched_mode_over_largest": tm / tl,
                            "max_rel_diff": float(np.max(np.abs(vm - vb) / np.abs(vb)))}
+    # mixed state (App. B.2 lhafmix): a 20-photon outcome of a 50-mode lossy state, the loop
+    # hafnian of the 100 x 100 matrix A with every occupied index pair repeated
+    ms_ = wl.lossy_state(seed=12, M=50, r_lo=0.8, r_hi=1.4, eta=0.6)
+    nm = wl.pattern_multinomial(np.random.default_rng(12), 50, 20, 3)
+    Tm, ndm, hm, _ = lg.plan(np.concatenate([nm, nm]))
+    ctx.gbs_pattern_prob_mixed(ms_.sigma, ms_.alpha, nm)
+    tmx = _timed(torch, lambda: ctx.gbs_pattern_prob_mixed(ms_.sigma, ms_.alpha, nm), reps=3)
+    out["mixed"] = {"workload": "P(n) of a 20-photon outcome (counts <= 3) of a 50-mode lossy state, eta = 0.6",
+                    "terms": Tm, "n_dim": ndm, "h": hm, "ms": tmx}
     # adjoint: one 32-photon outcome of a 40-mode state
     gb = wl.gradient_batch(seed=4, count=2)
     import time as _t

@@ -218,6 +218,18 @@ lhaf_status lhaf_grad(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128*
 lhaf_status gbs_pattern_prob(lhaf_ctx* ctx, int M, const lhaf_c128* U, const double* r, const lhaf_c128* alpha,
                              const int32_t* n, uint32_t flags, double* prob, lhaf_c128* lhaf_B);
 
+/* GBS pattern probability of a general (mixed) Gaussian state (App. A, Eq. mixed_prob): with the
+ * complex covariance sigma (2M x 2M in the basis (a_1..a_M, a_1^dag..a_M^dag), App. A) and the mean
+ * alpha, sigma_Q = sigma + I/2, A = X (I - sigma_Q^-1) (2M x 2M), gamma = alpha_full^dag
+ * sigma_Q^-1, P0 = exp(-alpha_full^dag sigma_Q^-1 alpha_full / 2) / sqrt(det sigma_Q), and
+ * P = Re(P0 lhaf(A_n)) / prod n_i!, where A_n repeats index i and i + M n_i times each (the
+ * repeated-pair sieve of App. B.2 over pairs of equal counts: prod (n_i + 1) terms, halved). This
+ * covers lossy states exactly, without a pure-state decomposition.
+ *   sigma: HOST 2M x 2M row-major; alpha: HOST M or NULL; n: HOST M; prob: HOST;
+ *   lhaf_A: HOST, optional (the loop hafnian of A_n). flags as for lhaf() (host pointers). */
+lhaf_status gbs_pattern_prob_mixed(lhaf_ctx* ctx, int M, const lhaf_c128* sigma, const lhaf_c128* alpha,
+                                   const int32_t* n, uint32_t flags, double* prob, lhaf_c128* lhaf_A);
+
 /* Host-side double-double sum of `count` partials (4 doubles each, as from lhaf_range) scaled
  * by 2^-h (exact). */
 lhaf_status lhaf_combine(int count, const double* partials_dd, int32_t h, lhaf_c128* out);

@@ -86,6 +86,8 @@ def _lib():
         L.lhaf_batched.restype = c.c_int
         L.gbs_pattern_prob.argtypes = [vp, c.c_int, vp, vp, vp, vp, c.c_uint32, ctypes.POINTER(c.c_double), vp]
         L.gbs_pattern_prob.restype = c.c_int
+        L.gbs_pattern_prob_mixed.argtypes = [vp, c.c_int, vp, vp, vp, c.c_uint32, ctypes.POINTER(c.c_double), vp]
+        L.gbs_pattern_prob_mixed.restype = c.c_int
         L.lhaf_grad.argtypes = [vp, c.c_int, vp, vp, vp, c.c_uint32, vp, vp, vp]
         L.lhaf_grad.restype = c.c_int
         L.lhaf_batched_plan_create.argtypes = [vp, c.c_int, c.c_int, vp, vp, vp, c.c_uint32, ctypes.POINTER(vp)]
@@ -337,6 +339,20 @@ class Context:
         _check(self._lib.gbs_pattern_prob(self._h, M, Uh.ctypes.data, rh.ctypes.data,
                                           None if ah is None else ah.ctypes.data, nh.ctypes.data, flags,
                                           ctypes.byref(prob), lh.ctypes.data), "gbs_pattern_prob")
+        return prob.value, complex(lh[0])
+
+    def gbs_pattern_prob_mixed(self, sigma, alpha, n, flags: int = 0):
+        """(P(n), lhaf(A_n)) for the Gaussian state with complex covariance sigma (2M x 2M) and mean
+        alpha (App. A, Eq. mixed_prob), mixed (lossy) states included."""
+        S = _host_c128(sigma)
+        M = S.shape[0] // 2
+        ah = None if alpha is None else _host_c128(alpha)
+        nh = _reps_arr(n, M)
+        prob = ctypes.c_double()
+        lh = np.zeros(1, np.complex128)
+        _check(self._lib.gbs_pattern_prob_mixed(self._h, M, S.ctypes.data, None if ah is None else ah.ctypes.data,
+                                                nh.ctypes.data, flags, ctypes.byref(prob), lh.ctypes.data),
+               "gbs_pattern_prob_mixed")
         return prob.value, complex(lh[0])
 
     def lhaf_grad(self, B, gamma=None, reps=None, flags: int = 0):

@@ -138,3 +138,68 @@ extern "C" lhaf_status gbs_pattern_prob(lhaf_ctx* ctx, int M, const lhaf_c128* U
   if (lhaf_B) *lhaf_B = lh;
   return LHAF_OK;
 }
+
+// GBS pattern probability of a general (mixed) Gaussian state (App. A, Eq. mixed_prob): the loop
+// hafnian of the 2M x 2M matrix A = X (I - sigma_Q^-1) with index i and i + M both repeated n_i
+// times (the repeated-pair sieve pairs them, App. B.2), loop weights gamma = alpha_full^dag
+// sigma_Q^-1, P = Re(P0 lhaf(A_n)) / prod n_i!.
+extern "C" lhaf_status gbs_pattern_prob_mixed(lhaf_ctx* ctx, int M, const lhaf_c128* sigma, const lhaf_c128* alpha,
+                                              const int32_t* n, uint32_t flags, double* prob, lhaf_c128* lhaf_A) {
+  if (!ctx || M <= 0 || !sigma || !n || !prob) return LHAF_EINVAL;
+  if (flags & LHAF_DEVICE_PTRS) return LHAF_EINVAL;  // host inputs only
+  const int M2 = 2 * M;
+  for (int i = 0; i < M; i++) {
+    if (n[i] < 0) return LHAF_EINVAL;
+    if (alpha && !(std::isfinite(alpha[i].re) && std::isfinite(alpha[i].im))) return LHAF_EINVAL;
+  }
+  for (size_t e = 0; e < (size_t)M2 * M2; e++)
+    if (!(std::isfinite(sigma[e].re) && std::isfinite(sigma[e].im))) return LHAF_EINVAL;
+  // sigma_Q = sigma + I/2, its inverse and determinant
+  std::vector<cd> lu((size_t)M2 * M2), inv;
+  for (int i = 0; i < M2; i++)
+    for (int j = 0; j < M2; j++) {
+      const lhaf_c128 z = sigma[(size_t)i * M2 + j];
+      lu[(size_t)i * M2 + j] = cd(z.re, z.im) + (i == j ? 0.5 : 0.0);
+    }
+  std::vector<int> piv;
+  cd phase;
+  double logdet;
+  if (!lu_factor(lu, M2, piv, phase, logdet)) return LHAF_EINVAL;
+  lu_inverse(lu, M2, piv, inv);
+  // A = X (I - sigma_Q^-1): row i of A is row (i + M) mod 2M of I - sigma_Q^-1
+  std::vector<lhaf_c128> A((size_t)M2 * M2);
+  for (int i = 0; i < M2; i++) {
+    const int r = (i + M) % M2;
+    for (int j = 0; j < M2; j++) {
+      const cd v = (r == j ? 1.0 : 0.0) - inv[(size_t)r * M2 + j];
+      A[(size_t)i * M2 + j] = {v.real(), v.imag()};
+    }
+  }
+  // gamma = alpha_full^dag sigma_Q^-1 and the quadratic form of P0
+  std::vector<cd> af(M2, 0.0);
+  for (int i = 0; i < M; i++) {
+    const cd a = alpha ? cd(alpha[i].re, alpha[i].im) : cd(0.0);
+    af[i] = a;
+    af[M + i] = std::conj(a);
+  }
+  std::vector<lhaf_c128> g(M2);
+  cd quad = 0.0;
+  for (int j = 0; j < M2; j++) {
+    cd gj = 0.0;
+    for (int i = 0; i < M2; i++) gj += std::conj(af[i]) * inv[(size_t)i * M2 + j];
+    g[j] = {gj.real(), gj.imag()};
+    quad += gj * af[j];
+  }
+  // P0 = exp(-quad / 2) / sqrt(det sigma_Q), det = phase * exp(logdet)
+  const cd P0 = std::exp(-0.5 * quad - 0.5 * logdet) / std::sqrt(phase);
+  std::vector<int32_t> reps2(M2);
+  for (int i = 0; i < M; i++) reps2[i] = reps2[M + i] = n[i];
+  lhaf_c128 lh;
+  const lhaf_status st = lhaf(ctx, M2, A.data(), g.data(), reps2.data(), flags & ~LHAF_DEVICE_PTRS, &lh, nullptr);
+  if (st != LHAF_OK) return st;
+  double log_fact = 0.0;
+  for (int i = 0; i < M; i++) log_fact += std::lgamma((double)n[i] + 1.0);
+  *prob = (P0 * cd(lh.re, lh.im)).real() * std::exp(-log_fact);
+  if (lhaf_A) *lhaf_A = lh;
+  return LHAF_OK;
+}

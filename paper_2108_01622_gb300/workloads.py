@@ -131,6 +131,33 @@ def lossy_kernel(rng, M: int, r_lo: float, r_hi: float, eta: float):
 
 
 @dataclass
+class MixedState:
+    sigma: np.ndarray  # 2M x 2M complex covariance in the basis (a_1..a_M, a_1^dag..a_M^dag)
+    alpha: np.ndarray  # M displacements
+    U: np.ndarray
+    r: np.ndarray
+    eta: float
+
+
+def lossy_state(seed: int, M: int, r_lo: float = 0.3, r_hi: float = 0.9, eta: float = 0.6,
+                alpha_mean_sq: float = 0.1) -> MixedState:
+    """A lossy displaced squeezed state as a covariance input: single-mode squeezing r ~ U[r_lo,
+    r_hi] (a -> a cosh r - a^dag sinh r), a Haar interferometer, then uniform transmission eta on
+    every mode, which maps the covariance to eta sigma + (1 - eta) I / 2 and the mean to
+    sqrt(eta) alpha. The displacement is complex normal before the loss."""
+    rng = np.random.default_rng(seed)
+    U = haar_unitary(rng, M)
+    r = rng.uniform(r_lo, r_hi, size=M)
+    ch, sh = np.diag(np.cosh(r)), np.diag(np.sinh(r))
+    Z = np.zeros((M, M))
+    S = np.block([[U, Z], [Z, U.conj()]]) @ np.block([[ch, -sh], [-sh, ch]])
+    sigma = 0.5 * S @ S.conj().T
+    sigma = eta * sigma + 0.5 * (1.0 - eta) * np.eye(2 * M)
+    alpha = np.sqrt(eta) * complex_normal(rng, M, alpha_mean_sq)
+    return MixedState(sigma.astype(complex), alpha.astype(complex), U, r, eta)
+
+
+@dataclass
 class Batch:
     B: np.ndarray  # shared M x M kernel
     gammas: List[np.ndarray]
