@@ -422,6 +422,29 @@ def run_extras(ctx, torch, dev, lg, wl):
     tmx = _timed(torch, lambda: ctx.gbs_pattern_prob_mixed(ms_.sigma, ms_.alpha, nm), reps=3)
     out["mixed"] = {"workload": "P(n) of a 20-photon outcome (counts <= 3) of a 50-mode lossy state, eta = 0.6",
                     "terms": Tm, "n_dim": ndm, "h": hm, "ms": tmx}
+    # eigenvalue-trace variant against the finite difference sieve (App. B.4, Fig. glynn_accuracy):
+    # relative error of lhaf(A1 (+) A2) against lhaf(A1) lhaf(A2) (halves by the sieve, each pair
+    # crossing the blocks), and the time of one N = 40 loop hafnian by each
+    acc = {}
+    for n_half in (12, 16, 20):
+        ef, ee = [], []
+        for sd in range(5):
+            bp = wl.block_diagonal_pair(seed=1000 * n_half + sd, n=n_half)
+            ones_h = [1] * n_half
+            ref = ctx.lhaf(bp.A1, None, ones_h) * ctx.lhaf(bp.A2, None, ones_h)
+            ones = [1] * (2 * n_half)
+            ef.append(abs(ctx.lhaf(bp.C, None, ones) - ref) / abs(ref))
+            ee.append(abs(ctx.lhaf(bp.C, None, ones, flags=lg.ET) - ref) / abs(ref))
+        acc[str(2 * n_half)] = {"fds_median": float(np.median(ef)), "fds_max": float(max(ef)),
+                                "et_median": float(np.median(ee)), "et_max": float(max(ee))}
+    bp = wl.block_diagonal_pair(seed=7, n=20)
+    ones = [1] * 40
+    tf = _timed(torch, lambda: ctx.lhaf(bp.C, None, ones), reps=3)
+    te_ = _timed(torch, lambda: ctx.lhaf(bp.C, None, ones, flags=lg.ET), reps=3)
+    out["et_vs_fds"] = {"workload": "block-diagonal A1 (+) A2 of random complex symmetric halves, loops on the "
+                                    "diagonal, one photon per index, 5 instances per N",
+                        "relative_error_by_N": acc, "fds_ms_N40": tf, "et_ms_N40": te_,
+                        "fds_terms_N40": lg.plan(ones)[0], "et_terms_N40": lg.plan(ones, flags=lg.ET)[0]}
     # adjoint: one 32-photon outcome of a 40-mode state
     gb = wl.gradient_batch(seed=4, count=2)
     import time as _t

@@ -67,6 +67,19 @@ typedef enum {
 #define LHAF_NO_ZERO_SPLIT 0x40u     /* evaluate the middle digits of even-eta pairs (delta' = 0) on
                                         the full working matrix instead of in zero-digit groups with
                                         those slots deleted (same sum; for comparisons) */
+#define LHAF_ET 0x80u                /* lhaf, lhaf_range, lhaf_plan, lhaf_plan_groups,
+                                        gbs_pattern_prob(_mixed): the eigenvalue-trace inclusion/
+                                        exclusion sum (App. B.1 Eq. ET_loop, read with the sign
+                                        (-1)^(h - |Z|); repeated pairs as in App. B.2) instead of the
+                                        finite difference sieve, for accuracy comparisons (App. B.4,
+                                        Fig. glynn_accuracy). Terms: every choice of kept pairs (at
+                                        least one) and of z_q in 1..eta_q copies of each, prod
+                                        (eta_q + 1) - 1 in all, on the shrunken matrix of the kept
+                                        pairs' slots; numbered by the number of kept pairs, then
+                                        by rank (lhaf_range uses this numbering; partials carry
+                                        the factor 2^h, so lhaf_combine applies unchanged).
+                                        Rejected (LHAF_EINVAL) by the batched calls, lhaf_grad
+                                        and lhaf_noalloc. */
 
 /* Compiled limits. */
 #define LHAF_MAX_DIM 64      /* working dimension n_dim = 2 * pairs (+1 loop border) */

@@ -27,6 +27,7 @@ NO_REPEAT_SPEEDUP = 0x8
 NO_LOOPS = 0x10
 BATCH_B_PER_ITEM = 0x20
 NO_ZERO_SPLIT = 0x40
+ET = 0x80  # eigenvalue-trace inclusion/exclusion instead of the finite difference sieve
 
 STATUS = {0: "LHAF_OK", 1: "LHAF_EINVAL", 2: "LHAF_ETOOBIG", 3: "LHAF_ECUDA", 4: "LHAF_ETIMEOUT",
           5: "LHAF_ENOMEM", 6: "LHAF_ECANCELLED"}
@@ -153,7 +154,8 @@ def plan(reps: Sequence[int], flags: int = 0, has_loops: bool = True) -> Tuple[i
 
 
 def plan_groups(reps: Sequence[int], flags: int = 0, has_loops: bool = True) -> int:
-    """Number of zero-digit groups the sieve runs as (0: a single sieve on the full matrix)."""
+    """Number of zero-digit groups the sieve runs as (0: a single sieve on the full matrix); with ET,
+    the number of support sizes."""
     r = np.ascontiguousarray(np.asarray(reps, dtype=np.int32))
     g = ctypes.c_int32()
     _check(_lib().lhaf_plan_groups(len(r), r.ctypes.data, flags, int(has_loops), ctypes.byref(g)), "lhaf_plan_groups")

@@ -116,9 +116,18 @@ extern "C" lhaf_status lhaf_ctx_create(lhaf_ctx** out, int device, void* cuda_st
   return LHAF_OK;
 }
 
-// Terms the sieve evaluates: the plan's, or the sum over its zero-digit groups.
+// Terms the sieve evaluates: the plan's, or the sum over its zero-digit groups, or over the
+// support sizes of the eigenvalue-trace form (0 when its counts overflow).
 static uint64_t evaluated_terms(const Plan& pl, uint32_t flags) {
   std::vector<Plan> subs;
+  if (flags & LHAF_ET) {
+    std::vector<unsigned long long> tab;
+    if (pl.N == 0) return pl.T;
+    if (!split_support_sizes(pl, subs, tab)) return 0;
+    uint64_t T = 0;
+    for (const Plan& s : subs) T += s.T;
+    return T;
+  }
   if (pl.N == 0 || (flags & LHAF_NO_ZERO_SPLIT) || !split_zero_digits(pl, subs)) return pl.T;
   uint64_t T = 0;
   for (const Plan& s : subs) T += s.T;
@@ -143,6 +152,11 @@ extern "C" lhaf_status lhaf_plan_groups(int M, const int32_t* reps, uint32_t fla
   lhaf_status st = build_plan(M, reps, flags, has_loops != 0, pl);
   if (st != LHAF_OK) return st;
   std::vector<Plan> subs;
+  if (flags & LHAF_ET) {
+    std::vector<unsigned long long> tab;
+    *groups = (pl.N > 0 && split_support_sizes(pl, subs, tab)) ? (int32_t)subs.size() : 0;
+    return LHAF_OK;
+  }
   *groups = (pl.N > 0 && !(flags & LHAF_NO_ZERO_SPLIT) && split_zero_digits(pl, subs)) ? (int32_t)subs.size() : 0;
   return LHAF_OK;
 }
@@ -399,7 +413,8 @@ namespace {
 // the staging buffer. Writes the unscaled dd partial to dd_dst and/or the value to val_dst.
 lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& subs, int M, const lhaf_c128* B,
                         const lhaf_c128* gamma, uint32_t flags, bool dev, uint64_t tb, uint64_t te, double* dd_dst,
-                        double2* val_dst, lhaf_stats* stats, bool timed) {
+                        double2* val_dst, lhaf_stats* stats, bool timed,
+                        const std::vector<unsigned long long>* et_tab = nullptr) {
   const bool fp32 = (flags & LHAF_FP32_TERMS) != 0;
   const char* env_stage = std::getenv("LHAF_STAGE");
   bool staged = pl.h <= kStageMaxDegree && !(env_stage && env_stage[0] == '0');
@@ -416,6 +431,8 @@ lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& 
     return (lhaf_status)record_cuda(cudaPeekAtLastError(), "cudaEventCreate");
   }
   const int nj = (int)subs.size();
+  const size_t et_bytes = et_tab ? sizeof(unsigned long long) * et_tab->size() : 0;
+  if (et_tab && (!w.et_table.reserve(et_bytes) || !w.h_et_table.reserve(et_bytes))) return LHAF_ENOMEM;
   if (!w.counter.reserve(sizeof(unsigned long long)) || !w.h_items.reserve(sizeof(BatchItem) * nj) ||
       !w.items.reserve(sizeof(BatchItem) * nj) ||
       !w.h_chunks.reserve(sizeof(long long) * (nj + 1)) || !w.chunks.reserve(sizeof(long long) * (nj + 1)))
@@ -435,6 +452,14 @@ lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& 
     jobs[j].base = base;
     jobs[j].src = 0;
     for (int q = 0; q < kMaxDim; q++) jobs[j].slot_mode[q] = q < 2 * sp.P ? sp.slot_mode[q] : -1;
+    if (et_tab) {
+      // eigenvalue-trace support size sp.P: terms read the full slot matrix, which is the last
+      // sieve's (all pairs kept), with the full pairs' counts
+      jobs[j].p.et_P = pl.P;
+      jobs[j].p.et_ndf = pl.nd;
+      jobs[j].p.et_table = static_cast<const unsigned long long*>(w.et_table.p);
+      for (int q = 0; q < pl.P; q++) jobs[j].p.eta[q] = pl.eta[q];
+    }
     bases[j] = base;
     base += sp.T;
     pool += (long long)sp.nd * sp.nd;
@@ -450,7 +475,14 @@ lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& 
   if (!w.chat.reserve(sizeof(double2) * std::max<long long>(pool, 1)) ||
       (fp32 && !w.chat32.reserve(sizeof(float2) * std::max<long long>(pool, 1))))
     return LHAF_ENOMEM;
-  uint64_t h2d = sizeof(BatchItem) * (uint64_t)nj;
+  if (et_tab) {
+    if (subs.back().P != pl.P) return LHAF_EINVAL;
+    for (int j = 0; j < nj; j++) jobs[j].p.et_off = jobs[nj - 1].chat_off - jobs[j].chat_off;
+    std::memcpy(w.h_et_table.p, et_tab->data(), et_bytes);
+    if (cudaMemcpyAsync(w.et_table.p, w.h_et_table.p, et_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return (lhaf_status)record_cuda(cudaPeekAtLastError(), "eigenvalue-trace rank table");
+  }
+  uint64_t h2d = sizeof(BatchItem) * (uint64_t)nj + et_bytes;
   int launches = 0;
   if (cudaMemcpyAsync(w.items.p, jobs, sizeof(BatchItem) * nj, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return (lhaf_status)record_cuda(cudaPeekAtLastError(), "group descriptors");
@@ -607,7 +639,10 @@ lhaf_status lhaf_common(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c12
   }
   if (stats) std::memset(stats, 0, sizeof(*stats));
   std::vector<Plan> subs;
-  const bool split = pl.N > 0 && !(flags & LHAF_NO_ZERO_SPLIT) && split_zero_digits(pl, subs);
+  std::vector<unsigned long long> et_tab;
+  const bool et = (flags & LHAF_ET) != 0;
+  if (et && pl.N > 0 && !split_support_sizes(pl, subs, et_tab)) return LHAF_ETOOBIG;
+  const bool split = et ? pl.N > 0 : (pl.N > 0 && !(flags & LHAF_NO_ZERO_SPLIT) && split_zero_digits(pl, subs));
   uint64_t T_eval = pl.T;
   if (split) {
     T_eval = 0;
@@ -642,7 +677,8 @@ lhaf_status lhaf_common(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c12
   double2* val_dst = ranged ? nullptr : (dev ? (double2*)out : (double2*)(ctx->d_out + 4));
   (void)fp32;
   if (!split) subs.assign(1, pl);  // one sieve on the full working matrix
-  st = run_grouped(ctx, pl, subs, M, B, gamma, flags, dev, tb, te, dd_dst, val_dst, stats, timed);
+  st = run_grouped(ctx, pl, subs, M, B, gamma, flags, dev, tb, te, dd_dst, val_dst, stats, timed,
+                   et ? &et_tab : nullptr);
   if (st != LHAF_OK) return st;
   if (stats) stats->d2h_bytes = dev ? 0 : 6 * sizeof(double);
   if (!dev) {

@@ -436,6 +436,7 @@ extern "C" lhaf_status lhaf_batched(lhaf_ctx* ctx, int batch, int M, const lhaf_
                                     const int32_t* reps, uint32_t flags, lhaf_c128* out, lhaf_status* item_status,
                                     lhaf_stats* stats) {
   if (!ctx || batch < 0 || M <= 0 || !B || !reps || (batch > 0 && !out)) return LHAF_EINVAL;
+  if (flags & LHAF_ET) return LHAF_EINVAL;  // the eigenvalue-trace variant runs through lhaf / lhaf_range
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (batch == 0) return LHAF_OK;
   const bool dev = (flags & LHAF_DEVICE_PTRS) != 0;
@@ -531,6 +532,7 @@ extern "C" lhaf_status lhaf_batched_plan_create(lhaf_ctx* ctx, int batch, int M,
   if (!plan) return LHAF_EINVAL;
   *plan = nullptr;
   if (!ctx || batch <= 0 || M <= 0 || !B || !reps) return LHAF_EINVAL;
+  if (flags & LHAF_ET) return LHAF_EINVAL;
   std::lock_guard<std::mutex> lock(ctx->mu);
   if (const cudaError_t e_ = (cudaSetDevice(ctx->device)); e_ != cudaSuccess)
     return (lhaf_status)record_cuda(e_, "cudaSetDevice");

@@ -69,15 +69,17 @@ struct BatchWork {
   DevBuf seg_item;   // per launch: the item of each segment (int)
   DevBuf item_h, acc, entries, chat, chat32, out, stage, wstage, in_B, in_gamma;
   DevBuf counter;    // chunk queue of a grouped launch (zeroed before each launch)
+  DevBuf et_table;   // eigenvalue-trace rank table of one loop hafnian
+  HostBuf h_et_table;
   HostBuf h_items, h_chunks, h_seg_begin, h_seg_item, h_item_h, h_chat, h_chat32, h_out, h_in;
   cudaEvent_t uploaded = nullptr;  // after the last copies that read the pinned buffers above
   void release() {
     if (uploaded) cudaEventDestroy(uploaded);
     uploaded = nullptr;
     for (DevBuf* b : {&items, &chunks, &seg_begin, &seg_item, &item_h, &acc, &entries, &chat, &chat32, &out, &stage,
-                      &wstage, &in_B, &in_gamma, &counter})
+                      &wstage, &in_B, &in_gamma, &counter, &et_table})
       b->release();
-    for (HostBuf* b : {&h_items, &h_chunks, &h_seg_begin, &h_seg_item, &h_item_h, &h_chat, &h_chat32, &h_out, &h_in})
+    for (HostBuf* b : {&h_et_table, &h_items, &h_chunks, &h_seg_begin, &h_seg_item, &h_item_h, &h_chat, &h_chat32, &h_out, &h_in})
       b->release();
   }
 };

@@ -19,7 +19,7 @@ using namespace lhafgpu;
 extern "C" lhaf_status lhaf_grad(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128* gamma, const int32_t* reps,
                                  uint32_t flags, lhaf_c128* value, lhaf_c128* dB, lhaf_c128* dgamma) {
   if (!ctx || M <= 0 || !B || !value) return LHAF_EINVAL;
-  if (flags & (LHAF_DEVICE_PTRS | LHAF_FP32_TERMS)) return LHAF_EINVAL;  // host inputs, FP64 only
+  if (flags & (LHAF_DEVICE_PTRS | LHAF_FP32_TERMS | LHAF_ET)) return LHAF_EINVAL;  // host inputs, FP64, sieve
   for (int i = 0; i < M; i++) {
     const int r = reps ? reps[i] : 1;
     if (r < 0) return LHAF_EINVAL;

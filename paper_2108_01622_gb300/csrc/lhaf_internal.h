@@ -36,8 +36,18 @@ struct TermParams {
   int stage_pad;                      // 1: stage out-of-range terms too, with weight 0
   int bq;                             // batched-mode self pair (its digit k gives delta' = bA - k), or -1
   int bA;                             // largest self-pair repeat of the batched mode
-  int pad2_;
+  // Eigenvalue-trace variant (App. B.1, B.2): et_P > 0 makes every term one choice of P = this
+  // sieve's pair count kept pairs out of the et_P pairs of the full slot matrix (et_ndf x et_ndf,
+  // at element offset et_off from this sieve's own), ranked through et_table (et_P + 1 squared
+  // entries, W[i][k] = e_k(eta_0..eta_{i-1}) over the full pairs, whose counts are in eta[]).
+  int et_P;
+  int et_ndf;
+  int pad3_;
+  long long et_off;
+  const unsigned long long* et_table;
 };
+
+static_assert(sizeof(TermParams) % 8 == 0, "TermParams is copied as 8-byte words");
 
 // One sieve of a grouped launch: a loop hafnian's whole sieve or one of its zero-digit groups.
 struct BatchItem {

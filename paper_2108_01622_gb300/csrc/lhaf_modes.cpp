@@ -41,7 +41,7 @@ extern "C" lhaf_status lhaf_batched_mode(lhaf_ctx* ctx, int M, const lhaf_c128* 
                                          const int32_t* reps, int mode, int n_cut, uint32_t flags, lhaf_c128* out,
                                          lhaf_stats* stats) {
   if (!ctx || M <= 0 || !B || !reps || !out || mode < 0 || mode >= M || n_cut < 0) return LHAF_EINVAL;
-  if (flags & (LHAF_DEVICE_PTRS | LHAF_FP32_TERMS | LHAF_NO_REPEAT_SPEEDUP)) return LHAF_EINVAL;
+  if (flags & (LHAF_DEVICE_PTRS | LHAF_FP32_TERMS | LHAF_NO_REPEAT_SPEEDUP | LHAF_ET)) return LHAF_EINVAL;
   if (reps[mode] != 0) return LHAF_EINVAL;
   if (stats) std::memset(stats, 0, sizeof(*stats));
   // the entries every outcome reads must be finite (the batched mode's row and loop included)

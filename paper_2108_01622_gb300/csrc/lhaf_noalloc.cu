@@ -91,6 +91,7 @@ extern "C" lhaf_status lhaf_noalloc(int device, void* cuda_stream, int M, const 
                                     const lhaf_c128* gamma, const int32_t* reps, uint32_t flags,
                                     lhaf_c128* out) {
   if (M <= 0 || !B || !out) return LHAF_EINVAL;
+  if (flags & LHAF_ET) return LHAF_EINVAL;  // the finite difference sieve only
   if (flags & LHAF_DEVICE_PTRS) flags &= ~LHAF_DEVICE_PTRS;  // always device pointers here
   const bool fp32 = (flags & LHAF_FP32_TERMS) != 0;
   cudaStream_t stream = (cudaStream_t)cuda_stream;

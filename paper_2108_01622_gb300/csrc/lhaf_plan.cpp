@@ -115,6 +115,49 @@ lhaf_status build_plan(int M, const int32_t* reps, uint32_t flags, bool loops, P
   return LHAF_OK;
 }
 
+bool split_support_sizes(const Plan& pl, std::vector<Plan>& subs, std::vector<unsigned long long>& table) {
+  subs.clear();
+  const int P = pl.P;
+  const unsigned long long lim = 1ull << 62;
+  table.assign((size_t)(P + 1) * (P + 1), 0ull);
+  table[0] = 1ull;  // W[0][0]: the empty choice
+  for (int i = 1; i <= P; i++) {
+    const unsigned long long e = (unsigned long long)pl.eta[i - 1];
+    for (int k = 0; k <= i; k++) {
+      const unsigned long long out = table[(size_t)(i - 1) * (P + 1) + k];
+      const unsigned long long in = k ? table[(size_t)(i - 1) * (P + 1) + k - 1] : 0ull;
+      if (in > lim / e || out > lim - in * e) return false;
+      table[(size_t)i * (P + 1) + k] = out + in * e;
+    }
+  }
+  if (pl.h > 1000) return false;  // 2^h must stay a finite double
+  for (int k = 1; k <= P; k++) {
+    Plan s;
+    s.M = pl.M;
+    s.N = pl.N;
+    s.h = pl.h;
+    s.H = pl.H;
+    s.bord = pl.bord;
+    s.P = k;
+    s.nd = 2 * k + pl.bord;
+    s.Hl = std::min(s.H, s.nd);
+    s.hp = -1;  // no sign symmetry: every term is evaluated
+    s.hp_even = 0;
+    s.wscale = std::ldexp(1.0, pl.h);
+    for (int q = 0; q < k; q++) {
+      s.slot_mode.push_back(pl.slot_mode[2 * q]);
+      s.slot_mode.push_back(pl.slot_mode[2 * q + 1]);
+      s.eta.push_back(pl.eta[q]);
+      s.radix.push_back(pl.eta[q] + 1);
+      s.skip.push_back(0);
+    }
+    s.T = table[(size_t)P * (P + 1) + k];
+    if (s.T == 0) continue;
+    subs.push_back(std::move(s));
+  }
+  return true;
+}
+
 bool split_zero_digits(const Plan& pl, std::vector<Plan>& subs) {
   subs.clear();
   std::vector<int> even;

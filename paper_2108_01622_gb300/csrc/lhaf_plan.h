@@ -38,6 +38,15 @@ lhaf_status build_plan(int M, const int32_t* reps, uint32_t flags, bool loops, P
 // h >= 1) and is dropped. Returns false (subs empty) when the plan has no even pair.
 bool split_zero_digits(const Plan& pl, std::vector<Plan>& subs);
 
+// Eigenvalue-trace form of a plan (App. B.1 Eq. ET_loop with the repeated pairs of App. B.2): the
+// terms are the choices of kept pairs S (|S| = k >= 1) with z_q in 1..eta_q copies of each; the
+// empty choice contributes nothing (f = 0 for h >= 1). One sieve per support size k = 1..P (subs[k-1]:
+// the first k pairs' slots, nd = 2k + bord, T = e_k(eta), no halving, wscale = 2^h so that the
+// common 2^-h scaling of the sieve sum gives the plain inclusion/exclusion sum); table receives
+// W[i][k] = e_k(eta_0..eta_{i-1}) for i, k = 0..P, row-major (P + 1) x (P + 1). False when a count
+// overflows 2^62.
+bool split_support_sizes(const Plan& pl, std::vector<Plan>& subs, std::vector<unsigned long long>& table);
+
 // Bordered slot matrix (nd x nd, row-major): [0][0] = 0; [0][1+s] = [1+s][0] = v_s (gamma of the
 // slot's mode, 1 for the pad); [b+s][b+t] = B[mode(s)][mode(t)] (0 when either is the pad), with B
 // read from its upper triangle.

@@ -422,9 +422,51 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
     const bool valid = t_raw >= p.t_lo && t_raw < p.t_end;
     const unsigned long long t = valid ? t_raw : p.t_begin;  // an idle team repeats a valid term
 
-    // ---- digits k_i of the term, delta'_i = eta_i - 2 k_i, and the weight (App. B.4) ----
-    // Lane q of the first warp of the team decodes digit q; the weight is a product over lanes.
-    if (G <= 32 || lt < 32) {
+    if (p.et_P > 0) {
+      // ---- eigenvalue-trace term (App. B.1 Eq. ET_loop, repeated pairs as in App. B.2) ----
+      // The term is one choice of P kept pairs out of et_P with z_q in 1..eta_q copies each; its
+      // rank t is unranked pair by pair from the last with the table W[i][k] = e_k(eta_0..
+      // eta_{i-1}), the number of such choices of k pairs among the first i (pair i-1 left out:
+      // ranks below W[i-1][k]; kept: z - 1 = quotient by W[i-1][k-1]). Kept pairs take compacted
+      // positions in ascending order: delta[c] = the pair's index, fdelta[c] = z. Weight
+      // prod C(eta_q, z_q) (-1)^(h - sum z) (the sign reading of Eq. ET_loop) times wscale.
+      if (lt == 0) {
+        const int PF = p.et_P;
+        const unsigned long long* Wt = p.et_table;
+        unsigned long long r = t;
+        int kk = P;
+        double wq = 1.0;
+        int zsum = 0;
+        for (int i = PF; i >= 1 && kk > 0; i--) {
+          const unsigned long long ex = Wt[(i - 1) * (PF + 1) + kk];
+          if (r < ex) continue;
+          r -= ex;
+          const unsigned long long w1 = Wt[(i - 1) * (PF + 1) + kk - 1];
+          if (w1 == 0ull) break;  // only for a rank out of range
+          unsigned long long zq;
+          if (r <= 0xffffffffull && w1 <= 0xffffffffull) {
+            zq = (unsigned)r / (unsigned)w1;
+          } else {
+            zq = r / w1;
+          }
+          r -= zq * w1;
+          const int z = 1 + (int)zq;
+          kk--;
+          ts->delta[kk] = i - 1;
+          ts->fdelta[kk] = (double)z;
+          wq *= binom_d(p.eta[i - 1], z);  // 0 when z > eta (only for a rank out of range)
+          zsum += z;
+        }
+        for (int c = 0; c < kk; c++) {  // unreachable for ranks in range; keeps indices valid
+          ts->delta[c] = c;
+          ts->fdelta[c] = 0.0;
+          wq = 0.0;
+        }
+        ts->weight = valid ? (((h - zsum) & 1) ? -wq : wq) * p.wscale : 0.0;
+      }
+    } else if (G <= 32 || lt < 32) {
+      // ---- digits k_i of the term, delta'_i = eta_i - 2 k_i, and the weight (App. B.4) ----
+      // Lane q of the first warp of the team decodes digit q; the weight is a product over lanes.
       double wq = 1.0;
       int par = 0;
       for (int q = lt; q < P; q += SG) {
@@ -468,7 +510,30 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
     // ---- working matrix K[i][j] = Chat[i][partner(j)] * delta_hat(j) ----
     // Column by column, so that the lanes of a team mostly share one column's factor and the FP64
     // multiplies issue only for columns whose |delta'| > 1 in some team of the warp.
-    {
+    if (p.et_P > 0) {
+      // eigenvalue-trace term: the kept pairs' slots of the full slot matrix (et_ndf x et_ndf at
+      // chat + et_off), columns scaled by the copies z (X_z of App. B.2)
+      const int ndf = p.et_ndf;
+      const V* fc = chat + p.et_off;
+      for (int w = lt; w < nd * nd; w += G) {
+        const int i = w / nd, j = w - (w / nd) * nd;
+        int fi = i, fj = j;
+        R f = (R)1;
+        if (i >= bord) {
+          const int s = i - bord;
+          fi = bord + 2 * ts->delta[s >> 1] + (s & 1);
+        }
+        if (j >= bord) {
+          const int s = j - bord;
+          fj = bord + 2 * ts->delta[s >> 1] + ((s & 1) ^ 1);
+          f = (R)ts->fdelta[s >> 1];
+        }
+        V c = fc[fi * ndf + fj];
+        c.x *= f;
+        c.y *= f;
+        W[i * ld + j] = c;
+      }
+    } else {
       const int sj = G / nd, si = G - (G / nd) * nd;
       int j = lt / nd, i = lt - (lt / nd) * nd;
       for (int w = lt; w < nd * nd; w += G) {

@@ -131,6 +131,32 @@ def lossy_kernel(rng, M: int, r_lo: float, r_hi: float, eta: float):
 
 
 @dataclass
+class BlockPair:
+    A1: np.ndarray  # n x n complex symmetric
+    A2: np.ndarray  # n x n complex symmetric
+    C: np.ndarray   # 2n x 2n: A1 on the even indices, A2 on the odd ones, no coupling between them
+
+
+def block_diagonal_pair(seed: int, n: int) -> BlockPair:
+    """Two random complex symmetric n x n matrices (entries (Z + Z^T)/2, Z complex normal with
+    E|Z_ij|^2 = 1) and their direct sum as one 2n x 2n matrix whose indices interleave the blocks
+    (index 2i is A1's i, 2i + 1 is A2's i), so that consecutive indices, which a one-photon-per-
+    mode pattern pairs, always belong to different blocks (the accuracy experiment of App. B.4,
+    Fig. glynn_accuracy: lhaf(C) = lhaf(A1) lhaf(A2), loops on the diagonal)."""
+    rng = np.random.default_rng(seed)
+
+    def sym():
+        Z = complex_normal(rng, (n, n), 1.0)
+        return (Z + Z.T) / 2
+
+    A1, A2 = sym(), sym()
+    C = np.zeros((2 * n, 2 * n), dtype=complex)
+    C[0::2, 0::2] = A1
+    C[1::2, 1::2] = A2
+    return BlockPair(A1, A2, C)
+
+
+@dataclass
 class MixedState:
     sigma: np.ndarray  # 2M x 2M complex covariance in the basis (a_1..a_M, a_1^dag..a_M^dag)
     alpha: np.ndarray  # M displacements

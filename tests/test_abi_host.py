@@ -91,6 +91,17 @@ def test_plan_groups_count(lg):
     assert lg.plan_groups([4]) == 1 and lg.plan([4])[0] == 1
 
 
+def test_et_plan_counts(lg):
+    # eigenvalue-trace form (App. B.1, B.2): every choice of kept pairs with 1..eta copies each,
+    # the empty one excepted; one sieve per number of kept pairs
+    for reps in ([1] * 10, [2, 1, 0, 3], [3, 3, 2, 2, 1], [4, 4, 4, 4]):
+        T, nd, h, P = lg.plan(reps, flags=lg.ET)
+        pairs, left = lo.matched_reps(reps)
+        etas = [e for _, _, e in pairs] + ([1] if left is not None else [])
+        assert T == math.prod(e + 1 for e in etas) - 1
+        assert lg.plan_groups(reps, flags=lg.ET) == P == len(etas)
+
+
 def test_zero_digit_groups_cover_every_digit_vector():
     # every digit vector lies in exactly one group: middle digits of the even pairs pick the group
     for etas in ([2], [2, 2], [4, 1, 2], [3, 2, 2, 1], [6, 4]):
