@@ -243,6 +243,28 @@ lhaf_status gbs_pattern_prob(lhaf_ctx* ctx, int M, const lhaf_c128* U, const dou
 lhaf_status gbs_pattern_prob_mixed(lhaf_ctx* ctx, int M, const lhaf_c128* sigma, const lhaf_c128* alpha,
                                    const int32_t* n, uint32_t flags, double* prob, lhaf_c128* lhaf_A);
 
+/* One step of the chain-rule sampler (App. A.2) for the pure state of gbs_pattern_prob: the
+ * distribution of the photon number of `mode` given the photon numbers n of the modes sampled so
+ * far and the coherent amplitudes beta of the modes still in the coherent-state basis, under the
+ * cutoff n_cut: cond[k] = P(n + k e_mode, beta) / sum_j P(n + j e_mode, beta), k = 0..n_cut, where
+ * P(n + k e_mode, beta) is proportional to |lhaf(B_{n + k e_mode})|^2 / k! with the loop weights
+ * gamma' of the displacement alpha - beta (App. A.2). The loop hafnians come from one
+ * lhaf_batched_mode call (App. B.5), or one lhaf_batched call over the n_cut + 1 patterns when
+ * ceil((N + n_cut)/2) is above its limit.
+ *   U, r, alpha: HOST, as for gbs_pattern_prob (alpha NULL = no displacement);
+ *   beta: HOST M or NULL (no coherent modes); beta[i] must be 0 for the modes already sampled in
+ *     photon number (beta[mode] is ignored: this step replaces it);
+ *   n: HOST M photon numbers (0 on coherent modes), n[mode] == 0;
+ *   u: a uniform number in [0, 1) to draw the outcome with (its inverse cumulative distribution),
+ *     or any value outside [0, 1) to draw nothing;
+ *   cond: HOST n_cut + 1; n_drawn: HOST or NULL, the drawn photon number (-1 if none was drawn or
+ *     every weight is 0, in which case cond is all zeros).
+ * flags: LHAF_PLAIN_ACCUM only. Errors: LHAF_EINVAL for bad arguments; the errors of the
+ * loop-hafnian calls. Synchronous. */
+lhaf_status gbs_chain_rule_step(lhaf_ctx* ctx, int M, const lhaf_c128* U, const double* r, const lhaf_c128* alpha,
+                                const lhaf_c128* beta, const int32_t* n, int mode, int n_cut, double u,
+                                uint32_t flags, double* cond, int32_t* n_drawn);
+
 /* Host-side double-double sum of `count` partials (4 doubles each, as from lhaf_range) scaled
  * by 2^-h (exact). */
 lhaf_status lhaf_combine(int count, const double* partials_dd, int32_t h, lhaf_c128* out);

@@ -89,6 +89,9 @@ def _lib():
         L.gbs_pattern_prob.restype = c.c_int
         L.gbs_pattern_prob_mixed.argtypes = [vp, c.c_int, vp, vp, vp, c.c_uint32, ctypes.POINTER(c.c_double), vp]
         L.gbs_pattern_prob_mixed.restype = c.c_int
+        L.gbs_chain_rule_step.argtypes = [vp, c.c_int, vp, vp, vp, vp, vp, c.c_int, c.c_int, c.c_double,
+                                          c.c_uint32, vp, ctypes.POINTER(c.c_int32)]
+        L.gbs_chain_rule_step.restype = c.c_int
         L.lhaf_grad.argtypes = [vp, c.c_int, vp, vp, vp, c.c_uint32, vp, vp, vp]
         L.lhaf_grad.restype = c.c_int
         L.lhaf_batched_plan_create.argtypes = [vp, c.c_int, c.c_int, vp, vp, vp, c.c_uint32, ctypes.POINTER(vp)]
@@ -356,6 +359,25 @@ class Context:
                                                 nh.ctypes.data, flags, ctypes.byref(prob), lh.ctypes.data),
                "gbs_pattern_prob_mixed")
         return prob.value, complex(lh[0])
+
+    def gbs_chain_rule_step(self, U, r, alpha, beta, n, mode: int, n_cut: int, u: float = -1.0, flags: int = 0):
+        """(cond, drawn): the distribution of the photon number of `mode` (0..n_cut) given the photon
+        numbers n and the coherent amplitudes beta of the other modes (App. A.2), and the outcome drawn
+        with the uniform number u (-1 when u is outside [0, 1))."""
+        Uh = _host_c128(U)
+        M = Uh.shape[0]
+        rh = np.ascontiguousarray(np.asarray(r, dtype=np.float64))
+        ah = None if alpha is None else _host_c128(alpha)
+        bh = None if beta is None else _host_c128(beta)
+        nh = _reps_arr(n, M)
+        cond = np.zeros(n_cut + 1, np.float64)
+        drawn = ctypes.c_int32(-1)
+        _check(self._lib.gbs_chain_rule_step(self._h, M, Uh.ctypes.data, rh.ctypes.data,
+                                             None if ah is None else ah.ctypes.data,
+                                             None if bh is None else bh.ctypes.data, nh.ctypes.data, int(mode),
+                                             int(n_cut), float(u), flags, cond.ctypes.data, ctypes.byref(drawn)),
+               "gbs_chain_rule_step")
+        return cond, drawn.value
 
     def lhaf_grad(self, B, gamma=None, reps=None, flags: int = 0):
         """(lhaf(B_n), dB (M x M, symmetric-variable derivative), dgamma (M,) or None)."""

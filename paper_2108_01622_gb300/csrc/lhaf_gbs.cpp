@@ -4,6 +4,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdint>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -65,21 +66,15 @@ void lu_inverse(const std::vector<cd>& lu, int n, const std::vector<int>& piv, s
   }
 }
 
-}  // namespace
-
-extern "C" lhaf_status gbs_pattern_prob(lhaf_ctx* ctx, int M, const lhaf_c128* U, const double* r,
-                                        const lhaf_c128* alpha, const int32_t* n, uint32_t flags, double* prob,
-                                        lhaf_c128* lhaf_B) {
-  if (!ctx || M <= 0 || !U || !r || !n || !prob) return LHAF_EINVAL;
-  if (flags & LHAF_DEVICE_PTRS) return LHAF_EINVAL;  // host inputs only
-  for (int i = 0; i < M; i++) {
-    if (n[i] < 0 || !std::isfinite(r[i])) return LHAF_EINVAL;
-    if (alpha && !(std::isfinite(alpha[i].re) && std::isfinite(alpha[i].im))) return LHAF_EINVAL;
-    for (int j = 0; j < M; j++)
-      if (!(std::isfinite(U[(size_t)i * M + j].re) && std::isfinite(U[(size_t)i * M + j].im))) return LHAF_EINVAL;
-  }
+// Pure-state kernel (App. A, Eq. Adef) of squeezed vacuum (a -> a cosh r - a^dag sinh r), the
+// interferometer a -> U a and the displacement alpha: the complex covariance sigma = S S^dag / 2,
+// sigma_Q = sigma + I/2, B = first block of A = X (I - sigma_Q^-1) = -(sigma_Q^-1)[M:2M, 0:M],
+// gamma = first M entries of alpha_full^dag sigma_Q^-1 and log P0 = -alpha_full^dag sigma_Q^-1
+// alpha_full / 2 - log(det sigma_Q) / 2. False if sigma_Q is singular.
+bool pure_state_kernel(int M, const lhaf_c128* U, const double* r, const std::vector<cd>& alpha,
+                       std::vector<lhaf_c128>& B, std::vector<lhaf_c128>& gB, double& logP0) {
   const int M2 = 2 * M;
-  // S = [[U, 0], [0, U*]] [[cosh r, -sinh r], [-sinh r, cosh r]]  (a -> a cosh r - a^dag sinh r, then U)
+  // S = [[U, 0], [0, U*]] [[cosh r, -sinh r], [-sinh r, cosh r]]
   std::vector<cd> S((size_t)M2 * M2, 0.0);
   for (int i = 0; i < M; i++)
     for (int j = 0; j < M; j++) {
@@ -90,7 +85,6 @@ extern "C" lhaf_status gbs_pattern_prob(lhaf_ctx* ctx, int M, const lhaf_c128* U
       S[(size_t)(M + i) * M2 + j] = -std::conj(u) * sh;
       S[(size_t)(M + i) * M2 + (M + j)] = std::conj(u) * ch;
     }
-  // sigma_Q = sigma + I/2 with sigma = S S^dag / 2  (App. A: complex covariance of the Q-function)
   std::vector<cd> sQ((size_t)M2 * M2, 0.0);
   for (int i = 0; i < M2; i++)
     for (int j = 0; j < M2; j++) {
@@ -102,24 +96,20 @@ extern "C" lhaf_status gbs_pattern_prob(lhaf_ctx* ctx, int M, const lhaf_c128* U
   std::vector<int> piv;
   cd phase;
   double logdet;
-  if (!lu_factor(lu, M2, piv, phase, logdet)) return LHAF_EINVAL;
+  if (!lu_factor(lu, M2, piv, phase, logdet)) return false;
   lu_inverse(lu, M2, piv, inv);
-  // A = X (I - sigma_Q^-1); for a pure state A = diag(B, B^*) and B = A[0:M, 0:M] = -(sigma_Q^-1)[M:2M, 0:M]
-  std::vector<lhaf_c128> B((size_t)M * M);
+  B.resize((size_t)M * M);
   for (int i = 0; i < M; i++)
     for (int j = 0; j < M; j++) {
       const cd v = -inv[(size_t)(M + i) * M2 + j];
       B[(size_t)i * M + j] = {v.real(), v.imag()};
     }
-  // gamma = alpha_full^dag sigma_Q^-1 with alpha_full = (alpha, alpha^*); gamma_B = its first M entries;
-  // P0 = exp(-1/2 alpha_full^dag sigma_Q^-1 alpha_full) / sqrt(det sigma_Q)
   std::vector<cd> af(M2, 0.0);
   for (int i = 0; i < M; i++) {
-    const cd a = alpha ? cd(alpha[i].re, alpha[i].im) : cd(0.0);
-    af[i] = a;
-    af[M + i] = std::conj(a);
+    af[i] = alpha[i];
+    af[M + i] = std::conj(alpha[i]);
   }
-  std::vector<lhaf_c128> gB(M);
+  gB.resize(M);
   cd quad = 0.0;
   for (int j = 0; j < M2; j++) {
     cd gj = 0.0;
@@ -127,7 +117,38 @@ extern "C" lhaf_status gbs_pattern_prob(lhaf_ctx* ctx, int M, const lhaf_c128* U
     if (j < M) gB[j] = {gj.real(), gj.imag()};
     quad += gj * af[j];
   }
-  const double logP0 = -0.5 * quad.real() - 0.5 * logdet;
+  logP0 = -0.5 * quad.real() - 0.5 * logdet;
+  return true;
+}
+
+bool finite_c(const lhaf_c128& z) { return std::isfinite(z.re) && std::isfinite(z.im); }
+
+lhaf_status validate_pure_state(int M, const lhaf_c128* U, const double* r, const lhaf_c128* alpha) {
+  for (int i = 0; i < M; i++) {
+    if (!std::isfinite(r[i])) return LHAF_EINVAL;
+    if (alpha && !finite_c(alpha[i])) return LHAF_EINVAL;
+    for (int j = 0; j < M; j++)
+      if (!finite_c(U[(size_t)i * M + j])) return LHAF_EINVAL;
+  }
+  return LHAF_OK;
+}
+
+}  // namespace
+
+extern "C" lhaf_status gbs_pattern_prob(lhaf_ctx* ctx, int M, const lhaf_c128* U, const double* r,
+                                        const lhaf_c128* alpha, const int32_t* n, uint32_t flags, double* prob,
+                                        lhaf_c128* lhaf_B) {
+  if (!ctx || M <= 0 || !U || !r || !n || !prob) return LHAF_EINVAL;
+  if (flags & LHAF_DEVICE_PTRS) return LHAF_EINVAL;  // host inputs only
+  for (int i = 0; i < M; i++)
+    if (n[i] < 0) return LHAF_EINVAL;
+  if (validate_pure_state(M, U, r, alpha) != LHAF_OK) return LHAF_EINVAL;
+  std::vector<cd> a(M, 0.0);
+  for (int i = 0; i < M; i++)
+    if (alpha) a[i] = cd(alpha[i].re, alpha[i].im);
+  std::vector<lhaf_c128> B, gB;
+  double logP0 = 0.0;
+  if (!pure_state_kernel(M, U, r, a, B, gB, logP0)) return LHAF_EINVAL;
   lhaf_c128 lh;
   const lhaf_status st = lhaf(ctx, M, B.data(), gB.data(), n, flags & ~LHAF_DEVICE_PTRS, &lh, nullptr);
   if (st != LHAF_OK) return st;
@@ -136,6 +157,83 @@ extern "C" lhaf_status gbs_pattern_prob(lhaf_ctx* ctx, int M, const lhaf_c128* U
   const double mag2 = lh.re * lh.re + lh.im * lh.im;
   *prob = mag2 > 0.0 ? std::exp(logP0 - log_fact + std::log(mag2)) : 0.0;
   if (lhaf_B) *lhaf_B = lh;
+  return LHAF_OK;
+}
+
+// One step of the chain-rule sampler (App. A.2): the photon number of `mode` conditioned on the
+// photon numbers n of the modes sampled so far and the coherent amplitudes beta of the modes still
+// in the coherent-state basis. The joint probability of (n with n_mode = k, beta) is that of the
+// photon pattern n + k e_mode with zeros on the coherent modes for the state displaced by -beta
+// (projecting on |beta> is counting no photons after the displacement D(-beta)), so it is
+// proportional to |lhaf(B_{n + k e_mode}, gamma')|^2 / k! with gamma' the loop weights of the
+// displacement alpha - beta (App. A.2); P0 and the other factorials cancel in the normalisation
+// over k = 0..n_cut. The n_cut + 1 loop hafnians come from one batched-mode call (App. B.5), or
+// from one batched call per outcome when its degree is above the batched mode's limit.
+extern "C" lhaf_status gbs_chain_rule_step(lhaf_ctx* ctx, int M, const lhaf_c128* U, const double* r,
+                                           const lhaf_c128* alpha, const lhaf_c128* beta, const int32_t* n,
+                                           int mode, int n_cut, double u, uint32_t flags, double* cond,
+                                           int32_t* n_drawn) {
+  if (!ctx || M <= 0 || !U || !r || !n || !cond || mode < 0 || mode >= M || n_cut < 0) return LHAF_EINVAL;
+  if (flags & ~(uint32_t)LHAF_PLAIN_ACCUM) return LHAF_EINVAL;
+  for (int i = 0; i < M; i++)
+    if (n[i] < 0 || (beta && !finite_c(beta[i]))) return LHAF_EINVAL;
+  if (n[mode] != 0 || !std::isfinite(u)) return LHAF_EINVAL;
+  if (validate_pure_state(M, U, r, alpha) != LHAF_OK) return LHAF_EINVAL;
+  std::vector<cd> a(M, 0.0);
+  for (int i = 0; i < M; i++) {
+    if (alpha) a[i] = cd(alpha[i].re, alpha[i].im);
+    if (beta && i != mode) a[i] -= cd(beta[i].re, beta[i].im);
+  }
+  std::vector<lhaf_c128> B, gB;
+  double logP0 = 0.0;
+  if (!pure_state_kernel(M, U, r, a, B, gB, logP0)) return LHAF_EINVAL;
+  std::vector<lhaf_c128> lh(n_cut + 1);
+  lhaf_status st = lhaf_batched_mode(ctx, M, B.data(), gB.data(), n, mode, n_cut, flags, lh.data(), nullptr);
+  if (st == LHAF_ETOOBIG) {
+    std::vector<int32_t> pats((size_t)(n_cut + 1) * M);
+    std::vector<lhaf_c128> gs((size_t)(n_cut + 1) * M);
+    for (int k = 0; k <= n_cut; k++)
+      for (int i = 0; i < M; i++) {
+        pats[(size_t)k * M + i] = i == mode ? k : n[i];
+        gs[(size_t)k * M + i] = gB[i];
+      }
+    std::vector<lhaf_status> item(n_cut + 1, LHAF_OK);
+    st = lhaf_batched(ctx, n_cut + 1, M, B.data(), gs.data(), pats.data(), flags, lh.data(), item.data(), nullptr);
+    for (int k = 0; st == LHAF_OK && k <= n_cut; k++)
+      if (item[k] != LHAF_OK) st = item[k];
+  }
+  if (st != LHAF_OK) return st;
+  // weights |lhaf|^2 / k!, normalised through logarithms (the magnitudes span many decades)
+  std::vector<double> lw(n_cut + 1, -INFINITY);
+  double lmax = -INFINITY;
+  for (int k = 0; k <= n_cut; k++) {
+    const double m2 = lh[k].re * lh[k].re + lh[k].im * lh[k].im;
+    if (!std::isfinite(m2)) return LHAF_EINVAL;
+    if (m2 > 0.0) lw[k] = std::log(m2) - std::lgamma((double)k + 1.0);
+    lmax = std::max(lmax, lw[k]);
+  }
+  double sum = 0.0;
+  for (int k = 0; k <= n_cut; k++) {
+    cond[k] = lmax > -INFINITY ? std::exp(lw[k] - lmax) : 0.0;
+    sum += cond[k];
+  }
+  int drawn = -1;
+  if (sum > 0.0) {
+    for (int k = 0; k <= n_cut; k++) cond[k] /= sum;
+    if (u >= 0.0 && u < 1.0) {
+      double c = 0.0;
+      drawn = n_cut;  // rounding of the cumulative sum: the last outcome with weight takes the rest
+      while (drawn > 0 && cond[drawn] == 0.0) drawn--;
+      for (int k = 0; k <= n_cut; k++) {
+        c += cond[k];
+        if (u < c) {
+          drawn = k;
+          break;
+        }
+      }
+    }
+  }
+  if (n_drawn) *n_drawn = drawn;
   return LHAF_OK;
 }
 
