@@ -45,6 +45,12 @@ struct TermParams {
   int pad3_;
   long long et_off;
   const unsigned long long* et_table;
+  // Several loop-weight vectors on one sieve (App. B.5, staged, no loop border): ng > 0 stages,
+  // besides d_M, the loop sequences s_k (k <= min(h, nd)) of each of the ng slot loop-weight
+  // vectors at gv (ng x nd, double2 on the slots), in rows h + g h + k - 1.
+  int ng;
+  int pad4_;
+  const void* gv;
 };
 
 static_assert(sizeof(TermParams) % 8 == 0, "TermParams is copied as 8-byte words");
@@ -96,6 +102,12 @@ cudaError_t launch_series_values(bool fp32, const void* stage, const double* wst
 cudaError_t launch_series_modes(bool fp32, const void* stage, const double* wstage, long long count,
                                 long long stage_ld, int h_max, int bord, int n_out, const int* h_out,
                                 const double* coef, int A, double* partials, cudaStream_t stream);
+// Several loop-weight vectors on shared terms (TermParams::ng): series of count staged terms for
+// each of ng vectors (grid y), partials[4 (g blocks + block)] with blocks = series_blocks(count).
+cudaError_t launch_series_multi(const void* stage, const double* wstage, long long count, long long stage_ld, int h,
+                                int kr, int ng, int plain, double* partials, cudaStream_t stream);
+// Shared bytes per team of the staged FP64 term kernel with the loop-vector buffers of ng > 0.
+size_t multi_team_bytes(int nd, int H);
 // acc[4 * seg_item[s]] += double-double sum of entries seg_begin[s] .. seg_begin[s+1]-1.
 cudaError_t launch_segment_reduce(const double* entries, const long long* seg_begin, const int* seg_item, int n_seg,
                                   int plain, double* acc, cudaStream_t stream);

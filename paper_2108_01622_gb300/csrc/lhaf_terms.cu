@@ -615,6 +615,7 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
       }
       const int r = row;
       const V ip = crecip(pv);  // issued before the swaps, so its latency overlaps them
+      if (STAGE && p.ng > 0 && ld > nd && lt == 0) W[k * ld + nd].x = (R)r;  // for the loop vectors
       // swap rows r and k+1 (columns k..nd-1), then columns r and k+1: a similarity transform
       for (int j = k + lt; j < nd; j += G) {
         const V a = W[r * ld + j], b = W[(k + 1) * ld + j];
@@ -712,6 +713,99 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
         }
       }
       team_sync<G>();
+    }
+
+    if constexpr (STAGE) {
+      if (G <= 32 && p.ng > 0 && bord == 0 && ld > nd) {
+        // ---- loop sequences of several loop-weight vectors on one Hessenberg form (App. B.5) ----
+        // M = C X_delta' = Q H Q^-1 with Q = P_0 L_0 P_1 L_1 ... (the swaps r_k recorded in the
+        // padding column, the multipliers l_i below the subdiagonal). For loop weights v (on the
+        // slots) and u = v X_delta', s_k = u M^(k-1) v^T = (u Q) H^(k-1) (Q^-1 v^T), k = 1..min(h, n),
+        // staged in rows h + g h + k - 1; the series kernel extends s_k past n with the
+        // characteristic polynomial (they are R_{k+1} of the bordered form).
+        V* xu = gX;
+        V* xa = xu + nd;
+        V* xb = xa + nd;
+        const V* gvs = reinterpret_cast<const V*>(p.gv);
+        const int kr = h < nd ? h : nd;
+        const bool st_col = valid || p.stage_pad;
+        const long long col = (long long)(t_raw - p.t_begin);
+        for (int g = 0; g < p.ng; g++) {
+          const V* vg = gvs + (size_t)g * nd;
+          for (int i = lt; i < nd; i += G) {
+            xa[i] = vg[i];
+            V c = vg[i ^ 1];
+            const int dl = ts->delta[i >> 1];
+            if (dl == -1) {
+              c.x = flip(c.x);
+              c.y = flip(c.y);
+            } else if (dl != 1) {
+              const R f = (R)ts->fdelta[i >> 1];
+              c.x *= f;
+              c.y *= f;
+            }
+            xu[i] = c;
+          }
+          team_sync<G>();
+          for (int k = 0; k < nd - 2; k++) {
+            const int r = (int)W[k * ld + nd].x;
+            if (lt == 0 && r > k + 1 && r < nd) {
+              const V a = xa[r];
+              xa[r] = xa[k + 1];
+              xa[k + 1] = a;
+              const V b = xu[r];
+              xu[r] = xu[k + 1];
+              xu[k + 1] = b;
+            }
+            team_sync<G>();
+            const V vk = xa[k + 1];
+            V su = zero;
+            for (int i = k + 2 + lt; i < nd; i += G) {
+              const V l = W[i * ld + k];
+              V a = xa[i];
+              cmsub(a, l, vk);
+              xa[i] = a;
+              cmac(su, xu[i], l);
+            }
+#pragma unroll
+            for (int off = SG / 2; off >= 1; off >>= 1) {
+              su.x += __shfl_xor_sync(0xffffffffu, su.x, off);
+              su.y += __shfl_xor_sync(0xffffffffu, su.y, off);
+            }
+            if (lt == 0) {
+              V a = xu[k + 1];
+              a.x += su.x;
+              a.y += su.y;
+              xu[k + 1] = a;
+            }
+            team_sync<G>();
+          }
+          V* x = xa;
+          V* y = xb;
+          for (int k = 1; k <= kr; k++) {
+            V d = zero;
+            for (int i = lt; i < nd; i += G) cmac(d, xu[i], x[i]);
+#pragma unroll
+            for (int off = SG / 2; off >= 1; off >>= 1) {
+              d.x += __shfl_xor_sync(0xffffffffu, d.x, off);
+              d.y += __shfl_xor_sync(0xffffffffu, d.y, off);
+            }
+            if (lt == 0 && st_col) stage[(long long)(h + g * h + k - 1) * stage_ld + col] = d;
+            if (k < kr) {
+              for (int i = lt; i < nd; i += G) {
+                V a = zero;
+                for (int j = (i > 0 ? i - 1 : 0); j < nd; j++) cmac(a, W[i * ld + j], x[j]);
+                y[i] = a;
+              }
+              team_sync<G>();
+              V* tmp = x;
+              x = y;
+              y = tmp;
+            }
+          }
+          team_sync<G>();
+        }
+      }
     }
 
     // ---- La Budde's recurrence, reverse (trailing blocks), truncated at degree Hl ----
@@ -1644,6 +1738,90 @@ __global__ void item_finalize_kernel(const double* __restrict__ acc, const int* 
   }
 }
 
+// Series of several loop-weight vectors on shared terms (App. B.5): thread (term tt, vector
+// g = blockIdx.y). d_M's coefficients a_m (rows 0..h-1) are the term's; the loop sequence s_k of
+// vector g (rows h + g h + k - 1, k <= kr = min(h, nd)) is R_{k+1} of the bordered form, continued
+// past kr by the characteristic polynomial: R_{k+1} = -sum_{i=1..k} a_i R_{k+1-i}. Then Newton,
+// z_k and e_k as in series_kernel; block partials at partials[4 (g blocks + block)].
+__global__ void __launch_bounds__(kSeriesThreads)
+series_multi_kernel(const double2* __restrict__ stage, const double* __restrict__ wstage, long long count,
+                    long long stage_ld, int h, int kr, int plain, double* __restrict__ partials) {
+  using V = double2;
+  extern __shared__ __align__(16) unsigned char smem[];
+  V* SR = reinterpret_cast<V*>(smem);             // (h + 2) x threads
+  V* Sp = SR + (size_t)(h + 2) * kSeriesThreads;  // (h + 1) x threads
+  V* Sz = Sp + (size_t)(h + 1) * kSeriesThreads;
+  V* Se = Sz + (size_t)(h + 1) * kSeriesThreads;
+  const int tid = threadIdx.x;
+  const int g = blockIdx.y;
+  const long long tt = (long long)blockIdx.x * kSeriesThreads + tid;
+  const V zero = make_double2(0.0, 0.0);
+  double fr = 0.0, fi = 0.0;
+  if (tt < count) {
+    auto A = [&](int m) -> V { return stage[(long long)(m - 1) * stage_ld + tt]; };
+    auto S = [&](int k) -> V { return stage[(long long)(h + g * h + k - 1) * stage_ld + tt]; };
+#define SIDX(i) ((size_t)(i) * kSeriesThreads + tid)
+    SR[SIDX(0)] = zero;
+    SR[SIDX(1)] = zero;  // R_1 = [t^1](d_M - d_K) = 0
+    Se[SIDX(0)] = make_double2(1.0, 0.0);
+    for (int k = 1; k <= h; k++) {
+      V sR = zero, sp = zero;
+      for (int i = 1; i <= k; i++) {
+        const V ai = A(i);
+        if (k > kr) cmac(sR, ai, SR[SIDX(k + 1 - i)]);
+        if (i < k) cmac(sp, ai, Sp[SIDX(k - i)]);
+      }
+      const V ak = A(k);
+      const double kk = (double)k;
+      const V Rk = (k <= kr) ? S(k) : make_double2(-sR.x, -sR.y);
+      const V pk = make_double2(-fma(kk, ak.x, sp.x), -fma(kk, ak.y, sp.y));
+      const V zk = make_double2(0.5 * fma(kk, Rk.x, pk.x), 0.5 * fma(kk, Rk.y, pk.y));
+      SR[SIDX(k + 1)] = Rk;
+      Sp[SIDX(k)] = pk;
+      Sz[SIDX(k)] = zk;
+      V se = zero;
+      for (int j = 1; j <= k; j++) cmac(se, Sz[SIDX(j)], Se[SIDX(k - j)]);
+      const double ik = 1.0 / kk;
+      Se[SIDX(k)] = make_double2(se.x * ik, se.y * ik);
+    }
+    const V f = Se[SIDX(h)];
+#undef SIDX
+    const double w = wstage[tt];
+    fr = f.x * w;
+    fi = f.y * w;
+  }
+  __shared__ double red[4][kSeriesThreads];
+  red[0][tid] = fr;
+  red[1][tid] = 0.0;
+  red[2][tid] = fi;
+  red[3][tid] = 0.0;
+  __syncthreads();
+  for (int off = kSeriesThreads / 2; off >= 1; off >>= 1) {
+    if (tid < off) {
+      double a = red[0][tid], b = red[1][tid], c = red[2][tid], d = red[3][tid];
+      if (plain) {
+        a += red[0][tid + off];
+        c += red[2][tid + off];
+      } else {
+        dd_add_dd(a, b, red[0][tid + off], red[1][tid + off]);
+        dd_add_dd(c, d, red[2][tid + off], red[3][tid + off]);
+      }
+      red[0][tid] = a;
+      red[1][tid] = b;
+      red[2][tid] = c;
+      red[3][tid] = d;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    double* o = partials + 4ll * ((long long)g * gridDim.x + blockIdx.x);
+    o[0] = red[0][0];
+    o[1] = red[1][0];
+    o[2] = red[2][0];
+    o[3] = red[3][0];
+  }
+}
+
 size_t series_shared_bytes(bool fp32, int h) {
   const size_t cs = fp32 ? sizeof(float2) : sizeof(double2);
   return (size_t)(4 * h + 5) * kSeriesThreads * cs;
@@ -1661,6 +1839,25 @@ cudaError_t launch_series(bool fp32, const void* stage, const double* wstage, lo
   void* args[] = {(void*)&stage, (void*)&wstage, (void*)&count, (void*)&stage_ld, (void*)&h,
                   (void*)&bord,  (void*)&plain,  (void*)&partials};
   return cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(kSeriesThreads), args, smem, stream);
+}
+
+cudaError_t launch_series_multi(const void* stage, const double* wstage, long long count, long long stage_ld, int h,
+                                int kr, int ng, int plain, double* partials, cudaStream_t stream) {
+  if (count <= 0 || ng <= 0) return cudaSuccess;
+  const size_t smem = series_shared_bytes(false, h);
+  const void* k = (const void*)series_multi_kernel;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long blocks = series_blocks(count);
+  void* args[] = {(void*)&stage, (void*)&wstage, (void*)&count, (void*)&stage_ld,
+                  (void*)&h,     (void*)&kr,     (void*)&plain, (void*)&partials};
+  return cudaLaunchKernel(k, dim3((unsigned)blocks, (unsigned)ng), dim3(kSeriesThreads), args, smem, stream);
+}
+
+size_t multi_team_bytes(int nd, int H) {
+  size_t b = team_shared_bytes(false, nd, H, 0, true) + ((sizeof(TeamScratch) + 15) & ~(size_t)15);
+  b += 3 * (size_t)nd * sizeof(double2);
+  return (b + 15) & ~(size_t)15;
 }
 
 cudaError_t launch_series_values(bool fp32, const void* stage, const double* wstage, long long count,
