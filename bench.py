@@ -413,6 +413,18 @@ def run_extras(ctx, torch, dev, lg, wl):
                            "batched_mode_ms": tm, "batched_patterns_ms": tbp, "speedup": tbp / tm,
                            "largest_outcome_alone_ms": tl, "batched_mode_over_largest": tm / tl,
                            "max_rel_diff": float(np.max(np.abs(vm - vb) / np.abs(vb)))}
+    # several loop-weight vectors on one pattern (App. B.5, threshold sub-detectors): 16 vectors on
+    # the 40-photon collision pattern, against the same 16 loop hafnians as one batch
+    pm_ = wl.collision_lhaf_40(seed=2)
+    Gm = wl.complex_normal(np.random.default_rng(21), (16, len(pm_.reps)))
+    Rm = np.repeat(np.asarray(pm_.reps)[None, :], 16, axis=0)
+    vm_ = ctx.lhaf_multi_gamma(pm_.B, Gm, pm_.reps)
+    vb_, _ = ctx.lhaf_batched(pm_.B, Gm, Rm)
+    tmg = _timed(torch, lambda: ctx.lhaf_multi_gamma(pm_.B, Gm, pm_.reps), reps=3)
+    tbg = _timed(torch, lambda: ctx.lhaf_batched(pm_.B, Gm, Rm), reps=3)
+    out["multi_gamma"] = {"workload": "16 loop-weight vectors on the 40-photon collision pattern (100-mode Haar)",
+                          "multi_gamma_ms": tmg, "batched_ms": tbg, "speedup": tbg / tmg,
+                          "max_rel_diff": float(np.max(np.abs(vm_ - vb_) / np.abs(vb_)))}
     # mixed state (App. B.2 lhafmix): a 20-photon outcome of a 50-mode lossy state, the loop
     # hafnian of the 100 x 100 matrix A with every occupied index pair repeated
     ms_ = wl.lossy_state(seed=12, M=50, r_lo=0.8, r_hi=1.4, eta=0.6)

@@ -206,6 +206,19 @@ void lhaf_batched_plan_destroy(lhaf_batch_plan* plan);
 lhaf_status lhaf_batched_mode(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128* gamma, const int32_t* reps,
                               int mode, int n_cut, uint32_t flags, lhaf_c128* out, lhaf_stats* stats);
 
+/* Loop hafnians of one pattern for several loop-weight vectors (App. A.2 threshold sub-detectors,
+ * App. B.5: only the diagonal of B_{n,beta} changes): out[g] = lhaf(B_n) with loops gamma_g. The
+ * sieve's per-term Hessenberg reduction and characteristic polynomial of the couplings are shared;
+ * each vector adds its loop sequence s_k = u M^(k-1) v^T from the Hessenberg form (O(h n^2)) and its
+ * series.
+ *   B: HOST M x M; gammas: HOST n_gamma x M (vector g at gammas + g*M); reps: HOST M;
+ *   out: HOST n_gamma. 1 <= n_gamma <= 256. flags: LHAF_PLAIN_ACCUM, LHAF_NO_REPEAT_SPEEDUP.
+ *   Errors: LHAF_EINVAL for bad arguments, LHAF_ETOOBIG when ceil(N/2) > 24 (the staged series
+ *   limit) or the working dimension exceeds LHAF_MAX_DIM. The middle digits of even-eta pairs
+ *   are evaluated on the full working matrix (no zero-digit groups). Synchronous. */
+lhaf_status lhaf_multi_gamma(lhaf_ctx* ctx, int M, const lhaf_c128* B, int n_gamma, const lhaf_c128* gammas,
+                             const int32_t* reps, uint32_t flags, lhaf_c128* out, lhaf_stats* stats);
+
 /* Value and gradient of lhaf(B_n) (the paper has no gradient; it follows from the definition, App.
  * B: the derivative of a matching sum with respect to one weight is the matching sum over the
  * remaining indices, e.g. d lhaf / d gamma_m = n_m lhaf(n - e_m)). Computed by a per-term adjoint

@@ -92,6 +92,8 @@ def _lib():
         L.gbs_chain_rule_step.argtypes = [vp, c.c_int, vp, vp, vp, vp, vp, c.c_int, c.c_int, c.c_double,
                                           c.c_uint32, vp, ctypes.POINTER(c.c_int32)]
         L.gbs_chain_rule_step.restype = c.c_int
+        L.lhaf_multi_gamma.argtypes = [vp, c.c_int, vp, c.c_int, vp, vp, c.c_uint32, vp, vp]
+        L.lhaf_multi_gamma.restype = c.c_int
         L.lhaf_grad.argtypes = [vp, c.c_int, vp, vp, vp, c.c_uint32, vp, vp, vp]
         L.lhaf_grad.restype = c.c_int
         L.lhaf_batched_plan_create.argtypes = [vp, c.c_int, c.c_int, vp, vp, vp, c.c_uint32, ctypes.POINTER(vp)]
@@ -378,6 +380,21 @@ class Context:
                                              int(n_cut), float(u), flags, cond.ctypes.data, ctypes.byref(drawn)),
                "gbs_chain_rule_step")
         return cond, drawn.value
+
+    def lhaf_multi_gamma(self, B, gammas, reps, flags: int = 0, stats: bool = False):
+        """lhaf(B_n) for each row of gammas (loop weights), sharing every sieve term's reduction and
+        characteristic polynomial (App. B.5, threshold sub-detectors)."""
+        Bh = _host_c128(B)
+        M = Bh.shape[0]
+        G = _host_c128(gammas).reshape(-1, M)
+        G = np.ascontiguousarray(G)
+        rh = _reps_arr(reps, M)
+        out = np.zeros(G.shape[0], np.complex128)
+        st = Stats()
+        _check(self._lib.lhaf_multi_gamma(self._h, M, Bh.ctypes.data, G.shape[0], G.ctypes.data, rh.ctypes.data,
+                                          flags, out.ctypes.data, ctypes.byref(st) if stats else None),
+               "lhaf_multi_gamma")
+        return (out, st.as_dict()) if stats else out
 
     def lhaf_grad(self, B, gamma=None, reps=None, flags: int = 0):
         """(lhaf(B_n), dB (M x M, symmetric-variable derivative), dgamma (M,) or None)."""

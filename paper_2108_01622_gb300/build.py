@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblhaf_gb300.so")
-SOURCES = ["lhaf_terms.cu", "lhaf_api.cpp", "lhaf_plan.cpp", "lhaf_probe.cu", "lhaf_noalloc.cu", "lhaf_batched.cpp", "lhaf_gbs.cpp", "lhaf_grad.cpp", "lhaf_modes.cpp"]
+SOURCES = ["lhaf_terms.cu", "lhaf_api.cpp", "lhaf_plan.cpp", "lhaf_probe.cu", "lhaf_noalloc.cu", "lhaf_batched.cpp", "lhaf_gbs.cpp", "lhaf_grad.cpp", "lhaf_modes.cpp", "lhaf_multi.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -49,7 +49,10 @@ def test_et_matches_oracle(ctx, lg, reps, loops):
     p = wl.small_problem(seed=len(reps) * 31 + sum(reps), M=len(reps), reps=reps, loops=loops)
     got = ctx.lhaf(p.B, p.gamma, list(reps), flags=lg.ET)
     ref = lo.lhaf_repeated(p.B, p.gamma, np.array(reps))
-    assert rel(got, ref) < TOL, (reps, loops, got, ref)
+    if ref == 0:  # odd N without loops: the inclusion/exclusion sum cancels to rounding level
+        assert abs(got) < 1e-12, (reps, loops, got)
+    else:
+        assert rel(got, ref) < TOL, (reps, loops, got, ref)
 
 
 def test_et_duplicated_matches_oracle_et(ctx, lg):
