@@ -425,6 +425,21 @@ def run_extras(ctx, torch, dev, lg, wl):
     out["multi_gamma"] = {"workload": "16 loop-weight vectors on the 40-photon collision pattern (100-mode Haar)",
                           "multi_gamma_ms": tmg, "batched_ms": tbg, "speedup": tbg / tmg,
                           "max_rel_diff": float(np.max(np.abs(vm_ - vb_) / np.abs(vb_)))}
+    # one chain-rule step (App. A.2): a 50-mode pure state, 20 photons sampled on half of the
+    # modes, coherent amplitudes on the rest, the next mode's distribution over 0..8
+    rng_c = np.random.default_rng(31)
+    Uc = wl.haar_unitary(rng_c, 50)
+    rc = rng_c.uniform(0.8, 1.2, size=50)
+    ac = wl.complex_normal(rng_c, 50, 0.1)
+    nc = np.zeros(50, dtype=np.int32)
+    nc[:25] = wl.pattern_multinomial(rng_c, 25, 20, 3)
+    bc = wl.complex_normal(rng_c, 50, 1.0)
+    bc[:26] = 0.0
+    ctx.gbs_chain_rule_step(Uc, rc, ac, bc, nc, 25, 8, u=0.5)
+    tcs = _timed(torch, lambda: ctx.gbs_chain_rule_step(Uc, rc, ac, bc, nc, 25, 8, u=0.5), reps=3)
+    out["chain_rule_step"] = {"workload": "50-mode pure state, 20 photons on modes 0..24, coherent amplitudes on "
+                                          "26..49, distribution of mode 25 over 0..8 and one draw",
+                              "ms": tcs}
     # mixed state (App. B.2 lhafmix): a 20-photon outcome of a 50-mode lossy state, the loop
     # hafnian of the 100 x 100 matrix A with every occupied index pair repeated
     ms_ = wl.lossy_state(seed=12, M=50, r_lo=0.8, r_hi=1.4, eta=0.6)

@@ -68,21 +68,24 @@ def test_batched_mode_gamma_none_and_n_cut_zero(ctx):
 
 
 def test_batched_mode_chain_rule_step_matches_single_calls(ctx, lg):
-    # a chain-rule step on the lossy 50-mode state: 20 photons fixed, the next mode batched to 8
+    # a chain-rule step on the lossy 50-mode state: 15 photons fixed, the next mode batched to 8.
+    # This item is well conditioned (sum |terms| / |sum| <= 160 over the outcomes), so the two
+    # exact sieves (the batched mode pairs the mode with itself, the single call pairs greedily)
+    # and the oracle agree to TOL. (On the 31-photon item of the same batch the ratio reaches
+    # 5.3e6 and the two sieves differ by up to ~5e-10, within their rounding.)
     b = wl.chain_rule_batch(seed=5, count=8)
-    reps = np.array(b.reps[0], dtype=np.int32)
-    gamma = np.array(b.gammas[0])
+    reps = np.array(b.reps[1], dtype=np.int32)
+    gamma = np.array(b.gammas[1])
     mode = int(np.nonzero(reps == 0)[0][0])
     n_cut = 8
     out, st = ctx.lhaf_batched_mode(b.B, gamma, reps, mode, n_cut, stats=True)
-    singles = []
     for n in range(n_cut + 1):
         r = reps.copy()
         r[mode] = n
-        singles.append(ctx.lhaf(b.B, gamma, r))
-        # two different exact sieves (the batched mode pairs the mode with itself, the single call
-        # pairs greedily), each within TOL of the value on these cancelling items
-        assert rel(out[n], singles[-1]) < 2 * TOL, (n, out[n], singles[-1])
+        single = ctx.lhaf(b.B, gamma, r)
+        ref = lo.lhaf_repeated(b.B, gamma, r)
+        assert rel(out[n], ref) < TOL, (n, out[n], ref)
+        assert rel(single, ref) < TOL, (n, single, ref)
     assert st["terms"] > 0 and st["launches"] >= 4
 
 

@@ -49,8 +49,10 @@ def test_et_matches_oracle(ctx, lg, reps, loops):
     p = wl.small_problem(seed=len(reps) * 31 + sum(reps), M=len(reps), reps=reps, loops=loops)
     got = ctx.lhaf(p.B, p.gamma, list(reps), flags=lg.ET)
     ref = lo.lhaf_repeated(p.B, p.gamma, np.array(reps))
-    if ref == 0:  # odd N without loops: the inclusion/exclusion sum cancels to rounding level
-        assert abs(got) < 1e-12, (reps, loops, got)
+    if ref == 0:
+        # odd N without loops: the exact value is 0 and the inclusion/exclusion sum (terms of
+        # order one here, entries ~0.5) cancels to rounding level, ~1e-12 at N = 11 with repeats
+        assert abs(got) < 1e-10, (reps, loops, got)
     else:
         assert rel(got, ref) < TOL, (reps, loops, got, ref)
 
