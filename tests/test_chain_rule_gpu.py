@@ -74,6 +74,17 @@ def test_step_with_coherent_modes(ctx, mode):
     np.testing.assert_allclose(cond, oracle_conditional(U, r, alpha, beta, n, mode, 7), rtol=1e-10, atol=1e-15)
 
 
+def test_uncoupled_modes_ignore_the_other_amplitude(ctx):
+    # with no interferometer the modes are independent: the photon number of mode 0 given any
+    # coherent amplitude of mode 1 follows the single-mode law of the squeezed, displaced mode 0
+    r = [0.6, 0.9]
+    alpha = [0.3 - 0.2j, 0.5j]
+    for beta1 in (0.0, 1.2 + 0.4j, -0.7j):
+        cond, _ = ctx.gbs_chain_rule_step(np.eye(2), r, alpha, [0.0, beta1], [0, 0], 0, 7)
+        ref = np.array([go.pattern_prob_pure(np.eye(1), r[:1], alpha[:1], [k])[0] for k in range(8)])
+        np.testing.assert_allclose(cond, ref / ref.sum(), rtol=1e-10, atol=1e-15)
+
+
 def test_draw_is_inverse_cdf(ctx):
     U, r, alpha = state(5, 3)
     n = [1, 0, 0]

@@ -267,6 +267,44 @@ def test_pure_equals_mixed_and_normalisation():
     assert p0 == pytest.approx(go.gbs_kernel(sigma, alpha)[2].real, rel=1e-12)
 
 
+@pytest.mark.parametrize("nbar", [0.3, 2.0])
+def test_mixed_thermal_mode_is_geometric(nbar):
+    # a thermal mode (sigma = (nbar + 1/2) I, App. A's complex covariance) counts k photons with
+    # probability nbar^k / (1 + nbar)^(k + 1): Eq. mixed_prob through the 2N x 2N matrix A_n
+    sigma = (nbar + 0.5) * np.eye(2, dtype=complex)
+    for k in range(6):
+        assert go.pattern_prob_mixed(sigma, [0.0], [k]) == pytest.approx(nbar ** k / (1 + nbar) ** (k + 1), rel=1e-12)
+
+
+def test_mixed_displaced_thermal_is_laguerre():
+    # displaced thermal light: P(k) = nbar^k / (1 + nbar)^(k+1) exp(-|a|^2 / (1 + nbar))
+    # L_k(-|a|^2 / (nbar (1 + nbar)))  (the photon statistics of a coherent signal in thermal noise)
+    special = pytest.importorskip("scipy.special")
+    nbar, a = 0.7, 0.5 + 0.6j
+    sigma = (nbar + 0.5) * np.eye(2, dtype=complex)
+    x = abs(a) ** 2
+    for k in range(6):
+        ref = nbar ** k / (1 + nbar) ** (k + 1) * math.exp(-x / (1 + nbar)) * special.eval_laguerre(
+            k, -x / (nbar * (1 + nbar)))
+        assert go.pattern_prob_mixed(sigma, [a], [k]) == pytest.approx(ref, rel=1e-11)
+
+
+def test_mixed_two_thermal_modes_factorise_and_lossy_state_normalises():
+    # independent thermal modes: the joint probability is the product of the geometric laws
+    sigma = np.diag([0.9, 1.6, 0.9, 1.6]).astype(complex)
+    for n in itertools.product(range(3), repeat=2):
+        ref = math.prod(nb ** k / (1 + nb) ** (k + 1) for nb, k in zip((0.4, 1.1), n))
+        assert go.pattern_prob_mixed(sigma, [0, 0], n) == pytest.approx(ref, rel=1e-12)
+    # a lossy squeezed, displaced two-mode state (uniform loss eta: sigma -> eta sigma + (1-eta)/2)
+    rng = np.random.default_rng(11)
+    U = _haar(rng, 2)
+    eta = 0.5
+    sig = eta * go.pure_state_sigma(U, [0.3, 0.2]) + 0.5 * (1 - eta) * np.eye(4)
+    alpha = np.sqrt(eta) * np.array([0.2 + 0.1j, -0.15j])
+    total = sum(go.pattern_prob_mixed(sig, alpha, n) for n in itertools.product(range(8), repeat=2))
+    assert total == pytest.approx(1.0, abs=1e-5)
+
+
 # --- planted mistakes: each must be caught by a pin above ---------------------------------
 
 
@@ -341,3 +379,39 @@ def test_planted_mistakes_are_caught(mutation, monkeypatch):
             return orig_et(A) * (-1) ** (N // 2)
         monkeypatch.setattr(lo, "lhaf_et", et2)
     assert not _pins_pass(), mutation
+
+
+def _mixed_pins_pass():
+    try:
+        test_mixed_thermal_mode_is_geometric(0.3)
+        test_mixed_displaced_thermal_is_laguerre()
+        test_mixed_two_thermal_modes_factorise_and_lossy_state_normalises()
+        return True
+    except AssertionError:
+        return False
+
+
+def test_mixed_pins_pass_unmutated():
+    assert _mixed_pins_pass()
+
+
+@pytest.mark.parametrize("mutation", ["no_half", "no_X", "gamma_no_conj", "P0_no_sqrt"])
+def test_mixed_planted_mistakes_are_caught(mutation, monkeypatch):
+    def kernel(sigma, alpha):
+        sigma = np.asarray(sigma, dtype=complex)
+        n2 = sigma.shape[0]
+        M = n2 // 2
+        alpha = np.asarray(alpha, dtype=complex)
+        af = np.concatenate([alpha, alpha.conj()])
+        sQ = sigma + (0.0 if mutation == "no_half" else 0.5) * np.eye(n2)
+        sQinv = np.linalg.inv(sQ)
+        O = np.eye(n2) - sQinv
+        X = np.block([[np.zeros((M, M)), np.eye(M)], [np.eye(M), np.zeros((M, M))]])
+        A = O if mutation == "no_X" else X @ O
+        gamma = (af if mutation == "gamma_no_conj" else af.conj()) @ sQinv
+        det = np.linalg.det(sQ)
+        P0 = np.exp(-0.5 * (af.conj() @ sQinv @ af)) / (det if mutation == "P0_no_sqrt" else np.sqrt(det))
+        return A, gamma, P0
+
+    monkeypatch.setattr(go, "gbs_kernel", kernel)
+    assert not _mixed_pins_pass()
