@@ -331,11 +331,17 @@ def run_extras(ctx, torch, dev, lg, wl):
     ms64 = _timed(torch, lambda: ctx.lhaf_range(B60, g60, p60.reps, 0, S), reps=2)
     ctx.lhaf_range(B60, g60, p60.reps, 0, 4096, flags=lg.FP32_TERMS)
     ms32 = _timed(torch, lambda: ctx.lhaf_range(B60, g60, p60.reps, 0, S, flags=lg.FP32_TERMS), reps=2)
+    msp = _timed(torch, lambda: ctx.lhaf_range(B60, g60, p60.reps, 0, S, flags=lg.PLAIN_ACCUM), reps=2)
+    pd = ctx.lhaf_range(p60.B, p60.gamma, p60.reps, 0, S)
+    pp = ctx.lhaf_range(p60.B, p60.gamma, p60.reps, 0, S, flags=lg.PLAIN_ACCUM)
+    sd, sp = complex(pd[0] + pd[1], pd[2] + pd[3]), complex(pp[0] + pp[1], pp[2] + pp[3])
     fl = lg.flops_per_term(nd60, h60, True)
     out["lhaf60"] = {"workload": "60-photon collision-free loop hafnian, 100-mode Haar, r~U[1.2,1.8], complex gamma",
                      "terms_per_lhaf": T60, "n_dim": nd60, "h": h60, "timed_terms": S,
                      "ms_per_60_photon_lhaf_projected": ms64 * T60 / S, "fp64_tflops": fl * S / (ms64 * 1e-3) / 1e12,
                      "fp32_terms_ms_per_lhaf_projected": ms32 * T60 / S, "fp32_speedup": ms64 / ms32,
+                     "plain_accum_ms_per_lhaf_projected": msp * T60 / S,
+                     "plain_vs_dd_slice_rel_diff": abs(sp - sd) / abs(sd),
                      "note": "projected = timed slice x (terms / slice); every term costs the same"}
     # batched vs one call per item: 512 loop hafnians of the chain-rule batch (N in 10..40)
     b = wl.chain_rule_batch(seed=3, count=512)
