@@ -723,79 +723,114 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
         // slots) and u = v X_delta', s_k = u M^(k-1) v^T = (u Q) H^(k-1) (Q^-1 v^T), k = 1..min(h, n),
         // staged in rows h + g h + k - 1; the series kernel extends s_k past n with the
         // characteristic polynomial (they are R_{k+1} of the bordered form).
-        V* xu = gX;
-        V* xa = xu + nd;
-        V* xb = xa + nd;
+        // Two vectors per pass (nv = 2, or 1 for the last of an odd count): the swaps and
+        // multipliers, and each H entry of the products, are loaded once for both.
+        V* xu = gX;           // u' of the pass's vectors, nd each
+        V* xa = xu + 2 * nd;  // Krylov vectors
+        V* xb = xa + 2 * nd;  // next Krylov vectors
         const V* gvs = reinterpret_cast<const V*>(p.gv);
         const int kr = h < nd ? h : nd;
         const bool st_col = valid || p.stage_pad;
         const long long col = (long long)(t_raw - p.t_begin);
-        for (int g = 0; g < p.ng; g++) {
-          const V* vg = gvs + (size_t)g * nd;
-          for (int i = lt; i < nd; i += G) {
-            xa[i] = vg[i];
-            V c = vg[i ^ 1];
+        for (int g0 = 0; g0 < p.ng; g0 += 2) {
+          const int nv = (p.ng - g0 >= 2) ? 2 : 1;
+          for (int w = lt; w < nv * nd; w += G) {
+            const int c = w >= nd ? 1 : 0;
+            const int i = w - c * nd;
+            const V* vg = gvs + (size_t)(g0 + c) * nd;
+            xa[c * nd + i] = vg[i];
+            V z = vg[i ^ 1];
             const int dl = ts->delta[i >> 1];
             if (dl == -1) {
-              c.x = flip(c.x);
-              c.y = flip(c.y);
+              z.x = flip(z.x);
+              z.y = flip(z.y);
             } else if (dl != 1) {
               const R f = (R)ts->fdelta[i >> 1];
-              c.x *= f;
-              c.y *= f;
+              z.x *= f;
+              z.y *= f;
             }
-            xu[i] = c;
+            xu[c * nd + i] = z;
           }
           team_sync<G>();
           for (int k = 0; k < nd - 2; k++) {
             const int r = (int)W[k * ld + nd].x;
-            if (lt == 0 && r > k + 1 && r < nd) {
-              const V a = xa[r];
-              xa[r] = xa[k + 1];
-              xa[k + 1] = a;
-              const V b = xu[r];
-              xu[r] = xu[k + 1];
-              xu[k + 1] = b;
+            if (lt < nv && r > k + 1 && r < nd) {  // lane c swaps vector c
+              V* a = xa + lt * nd;
+              V* b = xu + lt * nd;
+              const V ta = a[r];
+              a[r] = a[k + 1];
+              a[k + 1] = ta;
+              const V tb = b[r];
+              b[r] = b[k + 1];
+              b[k + 1] = tb;
             }
             team_sync<G>();
-            const V vk = xa[k + 1];
-            V su = zero;
+            const V vk0 = xa[k + 1];
+            const V vk1 = xa[nd + k + 1];
+            V su0 = zero, su1 = zero;
             for (int i = k + 2 + lt; i < nd; i += G) {
               const V l = W[i * ld + k];
-              V a = xa[i];
-              cmsub(a, l, vk);
-              xa[i] = a;
-              cmac(su, xu[i], l);
+              V a0 = xa[i];
+              cmsub(a0, l, vk0);
+              xa[i] = a0;
+              cmac(su0, xu[i], l);
+              if (nv == 2) {
+                V a1 = xa[nd + i];
+                cmsub(a1, l, vk1);
+                xa[nd + i] = a1;
+                cmac(su1, xu[nd + i], l);
+              }
             }
 #pragma unroll
             for (int off = SG / 2; off >= 1; off >>= 1) {
-              su.x += __shfl_xor_sync(0xffffffffu, su.x, off);
-              su.y += __shfl_xor_sync(0xffffffffu, su.y, off);
+              su0.x += __shfl_xor_sync(0xffffffffu, su0.x, off);
+              su0.y += __shfl_xor_sync(0xffffffffu, su0.y, off);
+              su1.x += __shfl_xor_sync(0xffffffffu, su1.x, off);
+              su1.y += __shfl_xor_sync(0xffffffffu, su1.y, off);
             }
             if (lt == 0) {
               V a = xu[k + 1];
-              a.x += su.x;
-              a.y += su.y;
+              a.x += su0.x;
+              a.y += su0.y;
               xu[k + 1] = a;
+              if (nv == 2) {
+                V b = xu[nd + k + 1];
+                b.x += su1.x;
+                b.y += su1.y;
+                xu[nd + k + 1] = b;
+              }
             }
             team_sync<G>();
           }
           V* x = xa;
           V* y = xb;
           for (int k = 1; k <= kr; k++) {
-            V d = zero;
-            for (int i = lt; i < nd; i += G) cmac(d, xu[i], x[i]);
+            V d0 = zero, d1 = zero;
+            for (int i = lt; i < nd; i += G) {
+              cmac(d0, xu[i], x[i]);
+              if (nv == 2) cmac(d1, xu[nd + i], x[nd + i]);
+            }
 #pragma unroll
             for (int off = SG / 2; off >= 1; off >>= 1) {
-              d.x += __shfl_xor_sync(0xffffffffu, d.x, off);
-              d.y += __shfl_xor_sync(0xffffffffu, d.y, off);
+              d0.x += __shfl_xor_sync(0xffffffffu, d0.x, off);
+              d0.y += __shfl_xor_sync(0xffffffffu, d0.y, off);
+              d1.x += __shfl_xor_sync(0xffffffffu, d1.x, off);
+              d1.y += __shfl_xor_sync(0xffffffffu, d1.y, off);
             }
-            if (lt == 0 && st_col) stage[(long long)(h + g * h + k - 1) * stage_ld + col] = d;
+            if (lt == 0 && st_col) {
+              stage[(long long)(h + g0 * h + k - 1) * stage_ld + col] = d0;
+              if (nv == 2) stage[(long long)(h + (g0 + 1) * h + k - 1) * stage_ld + col] = d1;
+            }
             if (k < kr) {
               for (int i = lt; i < nd; i += G) {
-                V a = zero;
-                for (int j = (i > 0 ? i - 1 : 0); j < nd; j++) cmac(a, W[i * ld + j], x[j]);
-                y[i] = a;
+                V a0 = zero, a1 = zero;
+                for (int j = (i > 0 ? i - 1 : 0); j < nd; j++) {
+                  const V hij = W[i * ld + j];
+                  cmac(a0, hij, x[j]);
+                  if (nv == 2) cmac(a1, hij, x[nd + j]);
+                }
+                y[i] = a0;
+                if (nv == 2) y[nd + i] = a1;
               }
               team_sync<G>();
               V* tmp = x;
@@ -1856,7 +1891,7 @@ cudaError_t launch_series_multi(const void* stage, const double* wstage, long lo
 
 size_t multi_team_bytes(int nd, int H) {
   size_t b = team_shared_bytes(false, nd, H, 0, true) + ((sizeof(TeamScratch) + 15) & ~(size_t)15);
-  b += 3 * (size_t)nd * sizeof(double2);
+  b += 6 * (size_t)nd * sizeof(double2);  // u', Krylov and next Krylov vectors of two loop vectors
   return (b + 15) & ~(size_t)15;
 }
 
