@@ -2,6 +2,8 @@
 60-photon workload against the oracle (FP64 path, and the FP32-term variant's stated error), and
 the paper's block-diagonal construction lhaf(diag(A1, A2)) = lhaf(A1) lhaf(A2) with every sieve
 pair crossing the blocks."""
+import os
+
 import numpy as np
 import pytest
 
@@ -25,6 +27,11 @@ def ctx():
     c = lg.Context(0)
     yield c
     c.close()
+
+
+@pytest.fixture(scope="module")
+def lg():
+    return ensure_built()
 
 
 def sub30():
@@ -69,3 +76,20 @@ def test_block_diagonal_identity_40_photons(ctx):
     err = abs(got - ref) / abs(ref)
     print(f"block-diagonal identity, 40 photons: relative error {err:.3e}")
     assert err <= 1e-10
+
+
+@pytest.mark.skipif(os.environ.get("LHAF_LONG_TESTS") != "1",
+                    reason="about 17 minutes on one GB300; set LHAF_LONG_TESTS=1 to run")
+def test_block_diagonal_identity_60_photons_sieve_and_eigenvalue_trace(ctx, lg):
+    # App. B.4, Fig. glynn_accuracy at the largest size: a whole 2^29-term sieve of working
+    # dimension 61 against the product of its 30-photon halves (oracle, FP64); the paper reports
+    # the sieve below 1e-8 up to N = 60. The eigenvalue-trace sum is run at N = 52 (2^26 terms).
+    for N, flags, bound in ((60, 0, 1e-8), (52, lg.ET, 1e-3)):
+        n = N // 2
+        bp = wl.block_diagonal_pair(seed=600 + N, n=n)
+        ref = lo.lhaf_repeated(bp.A1, np.diag(bp.A1).copy(), np.ones(n, np.int32)) * \
+            lo.lhaf_repeated(bp.A2, np.diag(bp.A2).copy(), np.ones(n, np.int32))
+        got = ctx.lhaf(bp.C, None, np.ones(N, np.int32), flags=flags)
+        err = abs(got - ref) / abs(ref)
+        print(f"block-diagonal, N = {N}, flags {flags}: relative error {err:.3e}")
+        assert err <= bound
