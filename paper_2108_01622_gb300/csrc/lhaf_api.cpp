@@ -139,7 +139,9 @@ extern "C" lhaf_status lhaf_plan(int M, const int32_t* reps, uint32_t flags, int
   Plan pl;
   lhaf_status st = build_plan(M, reps, flags, has_loops != 0, pl);
   if (st != LHAF_OK) return st;
-  if (terms) *terms = evaluated_terms(pl, flags);
+  const uint64_t T = evaluated_terms(pl, flags);
+  if (T == 0) return LHAF_ETOOBIG;  // eigenvalue-trace counts above 2^62
+  if (terms) *terms = T;
   if (n_dim) *n_dim = pl.nd;
   if (h) *h = pl.h;
   if (pairs) *pairs = pl.P;
