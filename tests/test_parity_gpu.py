@@ -171,6 +171,20 @@ def test_zero_digit_groups_match_full_matrix_and_oracle(ctx, lg, seed, loops):
     assert st["flops_model"] < st0["flops_model"]
 
 
+@pytest.mark.parametrize("force", ["0", "1"])
+def test_working_dimension_classes_same_value(ctx, lg, monkeypatch, force):
+    # the sieves of one loop hafnian launched in classes of equal working dimension (the default
+    # for large sieves) or all in one launch: the same value (the oracle's) either way, for the
+    # zero-digit groups and for the eigenvalue-trace sieves
+    monkeypatch.setenv("LHAF_ND_CLASSES", force)
+    p = wl.collision_lhaf_40(seed=22, n_modes=9, n_photons=19)
+    p.gamma = wl.complex_normal(np.random.default_rng(22), len(p.gamma))
+    ref = lo.lhaf_repeated(p.B, p.gamma, p.reps)
+    assert rel(ctx.lhaf(p.B, p.gamma, p.reps), ref) < TOL
+    q = wl.small_problem(seed=5, M=7, reps=(2, 1, 1, 3, 1, 2, 1), loops=True)
+    assert rel(ctx.lhaf(q.B, q.gamma, q.reps, flags=lg.ET), lo.lhaf_repeated(q.B, q.gamma, q.reps)) < TOL
+
+
 def test_zero_digit_range_partials_cross_groups(ctx, lg):
     p = wl.collision_lhaf_40(seed=12, n_modes=8, n_photons=16)
     p.gamma = wl.complex_normal(np.random.default_rng(3), len(p.gamma))
