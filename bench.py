@@ -460,7 +460,7 @@ def run_extras(ctx, torch, dev, lg, wl):
     # crossing the blocks), and the time of one N = 40 loop hafnian by each
     acc = {}
     for n_half in (12, 16, 20):
-        ef, ee = [], []
+        ef, ee, epl = [], [], []
         for sd in range(5):
             bp = wl.block_diagonal_pair(seed=1000 * n_half + sd, n=n_half)
             ones_h = [1] * n_half
@@ -468,7 +468,10 @@ def run_extras(ctx, torch, dev, lg, wl):
             ones = [1] * (2 * n_half)
             ef.append(abs(ctx.lhaf(bp.C, None, ones) - ref) / abs(ref))
             ee.append(abs(ctx.lhaf(bp.C, None, ones, flags=lg.ET) - ref) / abs(ref))
+            epl.append(abs(ctx.lhaf(bp.C, None, ones, flags=lg.PLAIN_ACCUM) - ref) / abs(ref))
         acc[str(2 * n_half)] = {"fds_median": float(np.median(ef)), "fds_max": float(max(ef)),
+                                "fds_plain_accum_median": float(np.median(epl)),
+                                "fds_plain_accum_max": float(max(epl)),
                                 "et_median": float(np.median(ee)), "et_max": float(max(ee))}
     bp = wl.block_diagonal_pair(seed=7, n=20)
     ones = [1] * 40
