@@ -538,26 +538,63 @@ lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& 
     if (!ensure_stage(ctx, (size_t)rows * cs * cap_cols, cap_cols)) staged = false;
   }
   const void* pool_ptr = fp32 ? w.chat32.p : w.chat.p;
-  int occ = 0;
-  const char* chatp = static_cast<const char*>(pool_ptr) + (size_t)jobs[rep].chat_off * cs;
-  const int team = pick_team(ctx, fp32, subs[order[rep]], staged, 2, chatp, &occ);
-  if (team == 0) return LHAF_ETOOBIG;
-  const int tpc = teams_per_cta(team);
-  if (staged && cap_cols < (uint64_t)tpc) return LHAF_ETOOBIG;  // a launch stages whole chunks
-  const size_t team_bytes = team_shared_bytes(fp32, nd_max, pl.H, P_max, staged);
-  const size_t items_bytes = cta_table_bytes(fp32, Hl_max, pl.H);
-  const size_t smem = items_bytes + (size_t)tpc * team_bytes;
-  if (smem > 227 * 1024) return LHAF_ETOOBIG;
-  const int occ_g = grouped_ctas_per_sm(fp32, team, smem, staged);
-  if (occ_g <= 0) return LHAF_ETOOBIG;
-  occ = ctas_per_sm_override(std::min(occ > 0 ? occ : occ_g, occ_g));
-  // chunks of tpc terms per group, and the chunk range covering [tb, te)
+  // launch classes: runs of sieves with one working dimension (one class when not by_class), each
+  // with the team size tuned on its costliest sieve, its shared memory and its occupancy
+  struct LaunchClass {
+    int j0, j1, team, tpc, occ;
+    long long c0, c1;
+    size_t team_bytes, items_bytes;
+  };
+  std::vector<LaunchClass> classes;
+  int team_rep = 0;  // the team of the class holding the costliest sieve (reported in stats)
   std::vector<long long> chunk_off(nj + 1, 0);
-  for (int j = 0; j < nj; j++) chunk_off[j + 1] = chunk_off[j] + (long long)((subs[order[j]].T + tpc - 1) / tpc);
+  for (int j0 = 0; j0 < nj;) {
+    int j1 = j0 + 1;
+    if (by_class)
+      while (j1 < nj && subs[order[j1]].nd == subs[order[j0]].nd) j1++;
+    else
+      j1 = nj;
+    int ndc = 0, Pc = 0, Hlc = 0, repc = j0;
+    double costc = -1.0;
+    for (int j = j0; j < j1; j++) {
+      const Plan& sj = subs[order[j]];
+      ndc = std::max(ndc, sj.nd);
+      Pc = std::max(Pc, sj.P);
+      Hlc = std::max(Hlc, sj.Hl);
+      const double c = lhaf_model_flops_per_term(sj.nd, sj.h, sj.bord) * (double)sj.T;
+      if (c > costc) {
+        costc = c;
+        repc = j;
+      }
+    }
+    LaunchClass lc;
+    lc.j0 = j0;
+    lc.j1 = j1;
+    int occ_t = 0;
+    const char* chatp = static_cast<const char*>(pool_ptr) + (size_t)jobs[repc].chat_off * cs;
+    lc.team = pick_team(ctx, fp32, subs[order[repc]], staged, 2, chatp, &occ_t);
+    if (lc.team == 0) return LHAF_ETOOBIG;
+    lc.tpc = teams_per_cta(lc.team);
+    if (staged && cap_cols < (uint64_t)lc.tpc) return LHAF_ETOOBIG;  // a launch stages whole chunks
+    lc.team_bytes = team_shared_bytes(fp32, ndc, pl.H, Pc, staged);
+    lc.items_bytes = cta_table_bytes(fp32, Hlc, pl.H);
+    const size_t smem_c = lc.items_bytes + (size_t)lc.tpc * lc.team_bytes;
+    if (smem_c > 227 * 1024) return LHAF_ETOOBIG;
+    const int occ_g = grouped_ctas_per_sm(fp32, lc.team, smem_c, staged);
+    if (occ_g <= 0) return LHAF_ETOOBIG;
+    lc.occ = ctas_per_sm_override(std::min(occ_t > 0 ? occ_t : occ_g, occ_g));
+    if (rep >= j0 && rep < j1) team_rep = lc.team;
+    // chunks of the class's tpc terms per sieve
+    for (int j = j0; j < j1; j++)
+      chunk_off[j + 1] = chunk_off[j] + (long long)((subs[order[j]].T + lc.tpc - 1) / lc.tpc);
+    classes.push_back(lc);
+    j0 = j1;
+  }
+  // the chunk range covering [tb, te) (one class when the range is partial)
   auto chunk_of = [&](uint64_t t) -> long long {  // chunk holding term t (t < T_all)
     int j = 0;
     while (j + 1 < nj && bases[j + 1] <= t) j++;
-    return chunk_off[j] + (long long)((t - bases[j]) / tpc);
+    return chunk_off[j] + (long long)((t - bases[j]) / classes[0].tpc);
   };
   long long kb = 0, ke = 0;
   if (by_class) {
@@ -565,6 +602,10 @@ lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& 
   } else if (te > tb) {
     kb = chunk_of(tb);
     ke = chunk_of(te - 1) + 1;
+  }
+  for (LaunchClass& lc : classes) {
+    lc.c0 = std::max<long long>(chunk_off[lc.j0], kb);
+    lc.c1 = std::min<long long>(chunk_off[lc.j1], ke);
   }
   long long* hco = static_cast<long long*>(w.h_chunks.p);
   std::memcpy(hco, chunk_off.data(), sizeof(long long) * (nj + 1));
@@ -574,58 +615,29 @@ lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& 
   if (cudaEventRecord(w.uploaded, s) != cudaSuccess)
     return (lhaf_status)record_cuda(cudaPeekAtLastError(), "cudaEventRecord");
 
-  // launch classes: runs of sieves with one working dimension (one class when not by_class)
-  struct LaunchClass {
-    long long c0, c1;
-    size_t team_bytes, items_bytes;
-    int occ;
-  };
-  std::vector<LaunchClass> classes;
-  for (int j0 = 0; j0 < nj;) {
-    int j1 = j0 + 1;
-    if (by_class)
-      while (j1 < nj && subs[order[j1]].nd == subs[order[j0]].nd) j1++;
-    else
-      j1 = nj;
-    int ndc = 0, Pc = 0, Hlc = 0;
-    for (int j = j0; j < j1; j++) {
-      ndc = std::max(ndc, subs[order[j]].nd);
-      Pc = std::max(Pc, subs[order[j]].P);
-      Hlc = std::max(Hlc, subs[order[j]].Hl);
-    }
-    LaunchClass lc;
-    lc.c0 = std::max<long long>(chunk_off[j0], kb);
-    lc.c1 = std::min<long long>(chunk_off[j1], ke);
-    lc.team_bytes = team_shared_bytes(fp32, ndc, pl.H, Pc, staged);
-    lc.items_bytes = cta_table_bytes(fp32, Hlc, pl.H);
-    const size_t smem_c = lc.items_bytes + (size_t)tpc * lc.team_bytes;
-    int occ_c = grouped_ctas_per_sm(fp32, team, smem_c, staged);
-    if (occ_c <= 0) return LHAF_ETOOBIG;
-    // the tuned occupancy holds for the representative sieve's class; the others take their limit
-    if (rep >= j0 && rep < j1) occ_c = std::min(occ_c, occ);
-    lc.occ = ctas_per_sm_override(occ_c);
-    if (lc.c1 > lc.c0 || classes.empty()) classes.push_back(lc);
-    j0 = j1;
-  }
   double* acc_dd = dd_dst ? dd_dst : ctx->d_out;
   if (timed) cudaEventRecord(ctx->ev0, s);
-  const long long span = staged ? std::max<long long>(1, (long long)(cap_cols / tpc)) : (ke - kb);
   int ci = 0;
+  bool first = true;
   for (size_t cl = 0; cl < classes.size(); cl++) {
     const LaunchClass& lc = classes[cl];
+    const bool last_class = cl + 1 == classes.size();
+    if (lc.c1 <= lc.c0 && !(first && last_class)) continue;  // nothing of the range in this class
+    first = false;
+    const long long span = staged ? std::max<long long>(1, (long long)(cap_cols / lc.tpc)) : (lc.c1 - lc.c0);
     const uint64_t max_ctas = (uint64_t)ctx->sms * (uint64_t)lc.occ;
     long long c0 = lc.c0;
     do {
-      const long long c1 = std::min<long long>(lc.c1, c0 + std::max<long long>(span, 1));
+      const long long c1 = std::max(c0, std::min<long long>(lc.c1, c0 + std::max<long long>(span, 1)));
       const long long n = c1 - c0;  // chunks in this launch
       long long nparts = 0;
       if (n > 0) {
         unsigned long long rounds = 1;
         const uint64_t grid = balanced_grid((uint64_t)n, 1, max_ctas, &rounds);
-        if (!staged && grid * (uint64_t)tpc > ctx->partial_cap) return LHAF_ETOOBIG;
+        if (!staged && grid * (uint64_t)lc.tpc > ctx->partial_cap) return LHAF_ETOOBIG;
         if (cudaMemsetAsync(w.counter.p, 0, sizeof(unsigned long long), s) != cudaSuccess)
           return (lhaf_status)record_cuda(cudaPeekAtLastError(), "chunk queue reset");
-        cudaError_t e = launch_grouped_terms(fp32, team, pool_ptr, (const BatchItem*)w.items.p, nj,
+        cudaError_t e = launch_grouped_terms(fp32, lc.team, pool_ptr, (const BatchItem*)w.items.p, nj,
                                              (const long long*)w.chunks.p, c0, c1, (int)grid, (int)rounds, tb, te,
                                              (int)lc.team_bytes, (int)lc.items_bytes, ctx->d_partials,
                                              staged ? ctx->d_stage : nullptr, staged ? ctx->d_wstage : nullptr,
@@ -634,22 +646,28 @@ lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& 
         if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "grouped terms kernel");
         launches++;
         if (staged) {
-          e = launch_series(fp32, ctx->d_stage, ctx->d_wstage, n * tpc, (long long)cap_cols, pl.h, pl.bord,
+          e = launch_series(fp32, ctx->d_stage, ctx->d_wstage, n * lc.tpc, (long long)cap_cols, pl.h, pl.bord,
                             (flags & LHAF_PLAIN_ACCUM) ? 1 : 0, ctx->d_partials, s);
           if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "series kernel");
           launches++;
-          nparts = series_blocks(n * tpc);
+          nparts = series_blocks(n * lc.tpc);
         } else {
-          nparts = (long long)grid * tpc;
+          nparts = (long long)grid * lc.tpc;
         }
       }
-      const bool last = cl + 1 == classes.size() && c1 >= lc.c1;
+      bool last = last_class && c1 >= lc.c1;
+      if (!last && c1 >= lc.c1) {  // the last class with chunks in the range ends the sum
+        last = true;
+        for (size_t k2 = cl + 1; k2 < classes.size(); k2++)
+          if (classes[k2].c1 > classes[k2].c0) last = false;
+      }
       cudaError_t e =
           launch_reduce(ctx->d_partials, nparts, pl.h, acc_dd, last ? val_dst : nullptr, s, ci > 0 ? 1 : 0);
       if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "reduction kernel");
       launches++;
       c0 = c1;
       ci++;
+      if (last) break;
     } while (c0 < lc.c1);
   }
   if (timed) cudaEventRecord(ctx->ev1, s);
@@ -664,7 +682,7 @@ lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& 
     stats->n_dim = nd_max;
     stats->h = pl.h;
     stats->pairs = pl.P;
-    stats->team = team;
+    stats->team = team_rep;
     stats->flops_model = flops;
     stats->kernel_ms = 0.0;
     stats->launches = launches;
