@@ -453,12 +453,14 @@ lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& 
     T_all += subs[j].T;
   }
   const char* env_cls = std::getenv("LHAF_ND_CLASSES");
+  // A whole sieve always runs largest working dimension first, so that the chunks left for the
+  // last wave of the queue are the cheapest ones.
   const bool big = T_all >= 2048ull * (uint64_t)std::max(ctx->sms, 1);
-  const bool by_class = nj > 1 && tb == 0 && te == T_all &&
-                        (env_cls ? env_cls[0] == '1' : big);  // LHAF_ND_CLASSES=0/1 forces it
+  const bool whole = nj > 1 && tb == 0 && te == T_all;
+  const bool by_class = whole && (env_cls ? env_cls[0] == '1' : big);  // LHAF_ND_CLASSES=0/1 forces it
   std::vector<int> order(nj);
   for (int j = 0; j < nj; j++) order[j] = j;
-  if (by_class)
+  if (whole)
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return subs[a].nd > subs[b].nd; });
   long long pool = 0;
   int nd_max = 0, P_max = 0, Hl_max = 0, rep = 0;
@@ -597,8 +599,8 @@ lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& 
     return chunk_off[j] + (long long)((t - bases[j]) / classes[0].tpc);
   };
   long long kb = 0, ke = 0;
-  if (by_class) {
-    ke = chunk_off[nj];  // the whole sieve (its sieves reordered by class)
+  if (whole) {
+    ke = chunk_off[nj];  // the whole sieve (its sieves reordered by working dimension)
   } else if (te > tb) {
     kb = chunk_of(tb);
     ke = chunk_of(te - 1) + 1;
