@@ -123,3 +123,12 @@ def test_rejects_bad_arguments(ctx, lg):
         with pytest.raises(lg.LhafError) as e:
             ctx.gbs_chain_rule_step(U, r, alpha, None, n, mode, 4)
         assert e.value.status == 1
+
+
+def test_cutoff_zero_and_vacuum_mode(ctx):
+    U, r, alpha = state(7, 3)
+    cond, drawn = ctx.gbs_chain_rule_step(U, r, alpha, None, [1, 0, 0], 2, 0, u=0.4)
+    assert cond.tolist() == [1.0] and drawn == 0
+    # a mode in vacuum (no squeezing, no displacement, no coupling) never holds a photon
+    cond, drawn = ctx.gbs_chain_rule_step(np.eye(2), [0.7, 0.0], [0.2, 0.0], None, [2, 0], 1, 5, u=0.99)
+    assert cond[0] == pytest.approx(1.0, abs=1e-15) and drawn == 0

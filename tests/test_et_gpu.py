@@ -110,3 +110,12 @@ def test_block_diagonal_accuracy_fds_vs_et(ctx, lg):
     assert max(err_fds) < 1e-11, err_fds
     assert max(err_et) < 1e-6, err_et
     assert np.median(err_fds) <= np.median(err_et), (err_fds, err_et)
+
+
+def test_et_degenerate_patterns(ctx, lg):
+    # empty pattern: 1; one photon: its loop weight (the pad pair); two photons of one mode: B_mm +
+    # gamma_m^2 (a pair or two loops)
+    p = wl.small_problem(seed=31, M=3, reps=(1, 0, 2), loops=True)
+    assert ctx.lhaf(p.B, p.gamma, [0, 0, 0], flags=lg.ET) == 1.0
+    assert rel(ctx.lhaf(p.B, p.gamma, [1, 0, 0], flags=lg.ET), p.gamma[0]) < TOL
+    assert rel(ctx.lhaf(p.B, p.gamma, [0, 0, 2], flags=lg.ET), p.B[2, 2] + p.gamma[2] ** 2) < TOL

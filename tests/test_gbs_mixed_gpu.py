@@ -105,3 +105,11 @@ def test_mixed_rejects_bad_arguments(ctx, lg):
     with pytest.raises(lg.LhafError) as e:
         ctx.gbs_pattern_prob_mixed(bad, st.alpha, [1, 1])
     assert e.value.status == 1
+
+
+def test_mixed_empty_pattern_is_vacuum_probability(ctx):
+    # no photon anywhere: P = P0 = exp(-alpha^dag sigma_Q^-1 alpha / 2) / sqrt(det sigma_Q)
+    st = wl.lossy_state(seed=4, M=3)
+    p, lh = ctx.gbs_pattern_prob_mixed(st.sigma, st.alpha, [0, 0, 0])
+    assert lh == 1.0
+    assert p == pytest.approx(go.gbs_kernel(st.sigma, st.alpha)[2].real, rel=1e-12)

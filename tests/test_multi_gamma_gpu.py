@@ -86,3 +86,14 @@ def test_multi_gamma_limits(ctx, lg):
     assert e.value.status == 2
     out = ctx.lhaf_multi_gamma(p.B, np.ones((3, 3), complex), [0, 0, 0])
     assert np.all(out == 1.0)
+
+
+def test_multi_gamma_vector_count_limit(ctx, lg):
+    p = wl.small_problem(seed=6, M=4, reps=(1, 1, 0, 1), loops=True)
+    G = wl.complex_normal(np.random.default_rng(6), (256, 4))
+    out = ctx.lhaf_multi_gamma(p.B, G, [1, 1, 0, 1])
+    for g in (0, 255):
+        assert rel(out[g], lo.lhaf_repeated(p.B, G[g], np.array([1, 1, 0, 1]))) < TOL
+    with pytest.raises(lg.LhafError) as e:
+        ctx.lhaf_multi_gamma(p.B, np.ones((257, 4), complex), [1, 1, 0, 1])
+    assert e.value.status == 1
