@@ -200,7 +200,9 @@ void lhaf_batched_plan_destroy(lhaf_batch_plan* plan);
  * the self pair's delta' in -A..A (A = floor(n_max/2)), so each term's Hessenberg reduction and
  * characteristic polynomial serve every outcome (its series gives all degrees up to the largest).
  *   B, gamma, reps: HOST, as for lhaf() (gamma NULL: loops from diag(B)); out: HOST, n_cut + 1.
- *   flags: LHAF_PLAIN_ACCUM only. Errors: LHAF_EINVAL for bad arguments or reps[mode] != 0;
+ *   The middle digits of the fixed pairs with even eta run as zero-digit groups (slots deleted,
+ *   as in lhaf) unless LHAF_NO_ZERO_SPLIT is given.
+ *   flags: LHAF_PLAIN_ACCUM, LHAF_NO_ZERO_SPLIT. Errors: LHAF_EINVAL for bad arguments or reps[mode] != 0;
  *   LHAF_ETOOBIG when ceil((N_fixed + n_cut)/2) exceeds 24 (the staged series limit) or the
  *   working dimension exceeds LHAF_MAX_DIM. Synchronous. */
 lhaf_status lhaf_batched_mode(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128* gamma, const int32_t* reps,

@@ -185,6 +185,86 @@ extern "C" lhaf_status lhaf_batched_mode(lhaf_ctx* ctx, int M, const lhaf_c128* 
     runs.push_back(std::move(cr));
   }
 
+  // Zero-digit groups of the fixed pairs (as for one loop hafnian): the middle digit of a fixed pair
+  // with even eta gives delta' = 0, whose two slots vanish from the term. For every subset Z of
+  // those pairs one sieve keeps Z at the middle digit with the slots deleted (constant weight
+  // factor C(eta, eta/2) (-1)^(eta/2)) and lets the other even fixed pairs skip it; each such
+  // group is closed under delta' -> -delta' and halves exactly on an odd fixed pair, else on an
+  // even one without its middle digit, else on the self pair.
+  if (!(flags & LHAF_NO_ZERO_SPLIT)) {
+    std::vector<ClassRun> split;
+    for (const ClassRun& cr : runs) {
+      const Plan& p = cr.pl;
+      std::vector<int> even;
+      for (int q = 0; q < p.P; q++)
+        if (q != cr.bq && p.eta[q] >= 2 && p.eta[q] % 2 == 0) even.push_back(q);
+      if (even.empty() || even.size() > 12) {
+        split.push_back(cr);
+        continue;
+      }
+      const int ne = (int)even.size();
+      for (uint32_t zmask = 0; zmask < (1u << ne); zmask++) {
+        std::vector<char> inZ(p.P, 0);
+        double ws = 1.0;
+        for (int b = 0; b < ne; b++)
+          if (zmask >> b & 1) {
+            const int q = even[b], e = p.eta[q];
+            inZ[q] = 1;
+            ws *= ((e / 2) % 2 ? -1.0 : 1.0) * binom_host(e, e / 2);
+          }
+        ClassRun sc;
+        sc.A = cr.A;
+        sc.outs = cr.outs;
+        Plan& g = sc.pl;
+        g.M = p.M;
+        g.N = p.N;
+        g.h = p.h;
+        g.H = p.H;
+        g.bord = p.bord;
+        g.wscale = ws;
+        for (int q = 0; q < p.P; q++) {
+          if (inZ[q]) continue;
+          if (q == cr.bq) sc.bq = (int)g.eta.size();
+          g.slot_mode.push_back(p.slot_mode[2 * q]);
+          g.slot_mode.push_back(p.slot_mode[2 * q + 1]);
+          g.eta.push_back(p.eta[q]);
+          g.skip.push_back((q != cr.bq && p.eta[q] % 2 == 0) ? 1 : 0);
+        }
+        g.P = (int)g.eta.size();
+        if (g.P == 0) continue;  // every remaining delta' is 0: f = 0 (h >= 1 here)
+        g.nd = 2 * g.P + g.bord;
+        g.Hl = std::min(g.H, g.nd);
+        int hp = -1;
+        for (int q = 0; q < g.P && hp < 0; q++)
+          if (q != sc.bq && g.eta[q] % 2 == 1) hp = q;
+        for (int q = 0; q < g.P && hp < 0; q++)
+          if (q != sc.bq && g.skip[q]) hp = q;
+        if (hp < 0) hp = sc.bq;
+        if (hp < 0) continue;  // unreachable: a remaining pair is odd, skips its middle or is the self pair
+        g.hp = hp;
+        g.hp_even = 0;
+        g.radix.resize(g.P);
+        uint64_t T = 1;
+        for (int q = 0; q < g.P; q++) {
+          int r;
+          if (q == sc.bq) {
+            r = (q == hp) ? sc.A + 1 : 2 * sc.A + 1;
+          } else if (q == hp) {
+            r = (g.eta[q] % 2) ? (g.eta[q] + 1) / 2 : g.eta[q] / 2;
+            g.skip[q] = 0;  // its digits k < eta/2 never reach the middle
+          } else {
+            r = g.eta[q] + 1 - g.skip[q];
+          }
+          g.radix[q] = r;
+          T *= (uint64_t)r;
+        }
+        g.T = T;
+        split.push_back(std::move(sc));
+      }
+    }
+    runs.swap(split);
+  }
+
   std::memcpy(w.h_item_h.p, item_h.data(), sizeof(int) * n_out_all);
   if (cudaMemsetAsync(w.acc.p, 0, sizeof(double) * 4 * n_out_all, s) != cudaSuccess ||
       cudaMemcpyAsync(w.item_h.p, w.h_item_h.p, sizeof(int) * n_out_all, cudaMemcpyHostToDevice, s) != cudaSuccess)

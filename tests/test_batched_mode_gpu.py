@@ -97,3 +97,17 @@ def test_batched_mode_rejects_bad_arguments(ctx, lg):
     with pytest.raises(lg.LhafError) as e:
         ctx.lhaf_batched_mode(p.B, p.gamma, [20, 20, 0], 2, 12)  # degree 26 > 24
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("reps,mode", [((2, 0, 2, 0, 1), 1), ((4, 2, 0, 2, 1, 1), 2), ((2, 2, 2, 0), 3)])
+def test_batched_mode_zero_digit_groups(ctx, lg, reps, mode):
+    # fixed pairs with even repeats: their middle digits run as zero-digit groups by default; the
+    # same outcomes with LHAF_NO_ZERO_SPLIT and from the oracle
+    p = wl.small_problem(seed=40 + sum(reps), M=len(reps), reps=reps, loops=True)
+    a = ctx.lhaf_batched_mode(p.B, p.gamma, list(reps), mode, 6)
+    b = ctx.lhaf_batched_mode(p.B, p.gamma, list(reps), mode, 6, flags=lg.NO_ZERO_SPLIT)
+    for n in range(7):
+        r = np.array(reps, dtype=np.int64)
+        r[mode] = n
+        ref = lo.lhaf_repeated(p.B, p.gamma, r)
+        assert rel(a[n], ref) < TOL and rel(b[n], ref) < TOL, (n, a[n], b[n], ref)
