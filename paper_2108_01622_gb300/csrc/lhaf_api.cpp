@@ -175,11 +175,6 @@ extern "C" lhaf_status lhaf_combine(int count, const double* p, int32_t h, lhaf_
   return LHAF_OK;
 }
 
-namespace {
-
-bool finite_c(const lhaf_c128& z) { return std::isfinite(z.re) && std::isfinite(z.im); }
-
-}  // namespace
 
 namespace lhafgpu {
 

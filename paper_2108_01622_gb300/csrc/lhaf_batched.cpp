@@ -30,8 +30,6 @@ using namespace lhafgpu;
 
 namespace {
 
-bool finite_c(const lhaf_c128& z) { return std::isfinite(z.re) && std::isfinite(z.im); }
-
 // Per-launch budget of staged coefficient rows (staged classes) or per-chunk partials (inline).
 constexpr size_t kLaunchBytes = (size_t)192 << 20;
 

@@ -9,10 +9,12 @@
 #include <vector>
 
 #include "../../include/lhaf.h"
+#include "lhaf_plan.h"
 
 namespace {
 
 using cd = std::complex<double>;
+using lhafgpu::finite_c;
 
 // In-place LU with partial pivoting of an n x n row-major matrix; returns false if singular.
 // log|det| and the sign/phase of det are accumulated.
@@ -121,7 +123,6 @@ bool pure_state_kernel(int M, const lhaf_c128* U, const double* r, const std::ve
   return true;
 }
 
-bool finite_c(const lhaf_c128& z) { return std::isfinite(z.re) && std::isfinite(z.im); }
 
 lhaf_status validate_pure_state(int M, const lhaf_c128* U, const double* r, const lhaf_c128* alpha) {
   for (int i = 0; i < M; i++) {

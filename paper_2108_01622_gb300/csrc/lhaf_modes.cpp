@@ -26,8 +26,6 @@ using namespace lhafgpu;
 
 namespace {
 
-bool finite_c(const lhaf_c128& z) { return std::isfinite(z.re) && std::isfinite(z.im); }
-
 double binom_host(int n, int k) {
   if (k < 0 || k > n) return 0.0;
   double c = 1.0;

@@ -23,8 +23,6 @@ using namespace lhafgpu;
 
 namespace {
 
-bool finite_c(const lhaf_c128& z) { return std::isfinite(z.re) && std::isfinite(z.im); }
-
 constexpr int kMaxGammaVectors = 256;
 
 }  // namespace

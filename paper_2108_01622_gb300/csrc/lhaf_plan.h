@@ -1,6 +1,7 @@
 // Host planner for the repeated-pair finite difference sieve (arXiv:2108.01622, App. B.2-B.4).
 #pragma once
 
+#include <cmath>
 #include <complex>
 #include <cstdint>
 #include <vector>
@@ -59,6 +60,9 @@ double lhaf_model_flops_per_term(int nd, int h, int bord);
 
 // Modelled FP64 lane utilisation (useful lane operations / issued lane slots) for team size G.
 double model_lane_efficiency(int nd, int Hl, int h, int bord, int G);
+
+// Both parts of a complex input finite (argument validation of the host entry points).
+inline bool finite_c(const lhaf_c128& z) { return std::isfinite(z.re) && std::isfinite(z.im); }
 
 inline void dd_add_dd_host(double& hi, double& lo, double bh, double bl) {
   const double s = hi + bh;
