@@ -33,7 +33,7 @@ WORKLOAD = ("collision-pattern loop hafnian: 100-mode Haar interferometer, r ~ U
 KERNEL_NAME = "grouped_terms_kernel (FP64 sieve terms of the zero-digit groups)"
 # DRAM bytes (read + write) of one grouped_terms_kernel launch on this workload, from the ncu
 # capture summarised in profiles/grouped_terms_kernel_collision40.md (None once the kernel changes)
-KERNEL_TRAFFIC_BYTES = 222208
+KERNEL_TRAFFIC_BYTES = 221696
 NOMINAL_FP64_GFLOPS = 152 * 4 * 0.5 * 2 * 2.070  # SMs x sub-partitions x FMA lanes/clk x 2 flops x GHz
 
 
