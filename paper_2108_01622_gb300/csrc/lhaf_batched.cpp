@@ -34,7 +34,7 @@ namespace {
 constexpr size_t kLaunchBytes = (size_t)192 << 20;
 
 // Working-dimension class bounds: a class holds the sieves with nd in (previous bound, bound].
-constexpr int kClassBounds[] = {8, 12, 16, 20, 24, 28, 32, 40, 48, 64};
+constexpr int kClassBounds[] = {8, 10, 12, 14, 16, 18, 20, 22, 24, 26, 28, 30, 32, 36, 40, 44, 48, 56, 64};
 constexpr int kNumBounds = (int)(sizeof(kClassBounds) / sizeof(kClassBounds[0]));
 
 struct GLaunch {
