@@ -14,6 +14,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -188,15 +189,21 @@ extern "C" lhaf_status lhaf_batched_mode(lhaf_ctx* ctx, int M, const lhaf_c128* 
   // those pairs one sieve keeps Z at the middle digit with the slots deleted (constant weight
   // factor C(eta, eta/2) (-1)^(eta/2)) and lets the other even fixed pairs skip it; each such
   // group is closed under delta' -> -delta' and halves exactly on an odd fixed pair, else on an
-  // even one without its middle digit, else on the self pair.
+  // even one without its middle digit, else on the self pair. Each group is its own launches and
+  // uploads, so classes below 256 terms per SM (where that overhead outweighs the smaller
+  // matrices: a 20-photon step ran 3.1 ms unsplit, 4.8 ms split) stay whole; LHAF_MODE_SPLIT=1 / 0
+  // forces the split on or off.
   if (!(flags & LHAF_NO_ZERO_SPLIT)) {
+    const char* env_split = std::getenv("LHAF_MODE_SPLIT");
+    const uint64_t min_T = 256ull * (uint64_t)std::max(ctx->sms, 1);
     std::vector<ClassRun> split;
     for (const ClassRun& cr : runs) {
       const Plan& p = cr.pl;
       std::vector<int> even;
       for (int q = 0; q < p.P; q++)
         if (q != cr.bq && p.eta[q] >= 2 && p.eta[q] % 2 == 0) even.push_back(q);
-      if (even.empty() || even.size() > 12) {
+      const bool want = env_split ? env_split[0] == '1' : p.T >= min_T;
+      if (even.empty() || even.size() > 12 || !want) {
         split.push_back(cr);
         continue;
       }

@@ -100,9 +100,10 @@ def test_batched_mode_rejects_bad_arguments(ctx, lg):
 
 
 @pytest.mark.parametrize("reps,mode", [((2, 0, 2, 0, 1), 1), ((4, 2, 0, 2, 1, 1), 2), ((2, 2, 2, 0), 3)])
-def test_batched_mode_zero_digit_groups(ctx, lg, reps, mode):
-    # fixed pairs with even repeats: their middle digits run as zero-digit groups by default; the
-    # same outcomes with LHAF_NO_ZERO_SPLIT and from the oracle
+def test_batched_mode_zero_digit_groups(ctx, lg, monkeypatch, reps, mode):
+    # fixed pairs with even repeats: their middle digits run as zero-digit groups (forced here; by
+    # default only for large sieves); the same outcomes with LHAF_NO_ZERO_SPLIT and from the oracle
+    monkeypatch.setenv("LHAF_MODE_SPLIT", "1")
     p = wl.small_problem(seed=40 + sum(reps), M=len(reps), reps=reps, loops=True)
     a = ctx.lhaf_batched_mode(p.B, p.gamma, list(reps), mode, 6)
     b = ctx.lhaf_batched_mode(p.B, p.gamma, list(reps), mode, 6, flags=lg.NO_ZERO_SPLIT)
