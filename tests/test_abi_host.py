@@ -102,6 +102,22 @@ def test_et_plan_counts(lg):
         assert lg.plan_groups(reps, flags=lg.ET) == P == len(etas)
 
 
+def test_et_plan_counts_random_patterns(lg):
+    # the eigenvalue-trace term count over many random patterns: prod (eta + 1) - 1 over the
+    # oracle's greedy pairs (a pad pair for odd N), one sieve per number of kept pairs
+    rng = np.random.default_rng(17)
+    for _ in range(200):
+        M = int(rng.integers(1, 9))
+        reps = [int(x) for x in rng.integers(0, 5, size=M)]
+        if sum(reps) == 0:
+            continue
+        pairs, left = lo.matched_reps(reps)
+        etas = [e for _, _, e in pairs] + ([1] if left is not None else [])
+        T, nd, h, P = lg.plan(reps, flags=lg.ET)
+        assert T == math.prod(e + 1 for e in etas) - 1, reps
+        assert P == len(etas) and lg.plan_groups(reps, flags=lg.ET) == P
+
+
 def test_zero_digit_groups_cover_every_digit_vector():
     # every digit vector lies in exactly one group: middle digits of the even pairs pick the group
     for etas in ([2], [2, 2], [4, 1, 2], [3, 2, 2, 1], [6, 4]):
