@@ -113,3 +113,14 @@ def test_mixed_empty_pattern_is_vacuum_probability(ctx):
     p, lh = ctx.gbs_pattern_prob_mixed(st.sigma, st.alpha, [0, 0, 0])
     assert lh == 1.0
     assert p == pytest.approx(go.gbs_kernel(st.sigma, st.alpha)[2].real, rel=1e-12)
+
+
+def test_mixed_by_inclusion_exclusion_lhafmix(ctx, lg):
+    # the paper's lhafmix form (inclusion/exclusion over included copies, LHAF_ET) gives the same
+    # probability as the default sieve and the oracle
+    st = wl.lossy_state(seed=13, M=4)
+    for n in ([1, 2, 0, 1], [2, 0, 2, 1]):
+        p_et, _ = ctx.gbs_pattern_prob_mixed(st.sigma, st.alpha, n, flags=lg.ET)
+        p_fds, _ = ctx.gbs_pattern_prob_mixed(st.sigma, st.alpha, n)
+        ref = go.pattern_prob_mixed(st.sigma, st.alpha, n)
+        assert p_et == pytest.approx(ref, rel=1e-10) and p_fds == pytest.approx(ref, rel=1e-10)
