@@ -183,6 +183,10 @@ def test_working_dimension_classes_same_value(ctx, lg, monkeypatch, force):
     assert rel(ctx.lhaf(p.B, p.gamma, p.reps), ref) < TOL
     q = wl.small_problem(seed=5, M=7, reps=(2, 1, 1, 3, 1, 2, 1), loops=True)
     assert rel(ctx.lhaf(q.B, q.gamma, q.reps, flags=lg.ET), lo.lhaf_repeated(q.B, q.gamma, q.reps)) < TOL
+    # degree 25: the series run inline in the terms kernel (no staging), 16 zero-digit groups
+    # (a well-conditioned instance: sum |terms| / |sum| = 3.9e3)
+    u = wl.small_problem(seed=2, M=8, reps=(8, 8, 8, 8, 6, 6, 4, 2), loops=True, scale=1.0)
+    assert rel(ctx.lhaf(u.B, u.gamma, u.reps), lo.lhaf_repeated(u.B, u.gamma, u.reps)) < TOL
 
 
 def test_zero_digit_range_partials_cross_groups(ctx, lg):
