@@ -24,6 +24,25 @@ def test_exports_every_declared_function(lg):
     assert not missing, missing
 
 
+def test_header_is_plain_c(tmp_path):
+    # the boundary is a C ABI: the header compiles as strict C99 (and as C++), no torch types
+    import os
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "abi.c"
+    src.write_text('#include "include/lhaf.h"\nint main(void) { lhaf_stats s; (void)s; return 0; }\n')
+    for lang, std in (("c", "-std=c99"), ("c++", "-std=c++17")):
+        r = subprocess.run([gcc, std, "-Wall", "-Wextra", "-Werror", "-pedantic", "-x", lang, "-I", root, "-c",
+                            str(src), "-o", str(tmp_path / f"abi_{lang}.o")], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+    text = open(os.path.join(root, "include", "lhaf.h")).read()
+    assert "Tensor" not in text and "at::" not in text and "torch::" not in text
+
+
 def halved_count(reps, loops):
     """Evaluated terms after the sign-symmetry halving, from the oracle's greedy pairs."""
     pairs, leftover = lo.matched_reps(reps)
