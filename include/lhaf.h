@@ -214,9 +214,10 @@ lhaf_status lhaf_batched_mode(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lh
  * each vector adds its loop sequence s_k = u M^(k-1) v^T from the Hessenberg form (O(h n^2)) and its
  * series.
  *   B: HOST M x M; gammas: HOST n_gamma x M (vector g at gammas + g*M); reps: HOST M;
- *   out: HOST n_gamma. 1 <= n_gamma <= 256. flags: LHAF_PLAIN_ACCUM, LHAF_NO_REPEAT_SPEEDUP.
- *   Errors: LHAF_EINVAL for bad arguments, LHAF_ETOOBIG when ceil(N/2) > 24 (the staged series
- *   limit) or the working dimension exceeds LHAF_MAX_DIM. The middle digits of even-eta pairs
+ *   out: HOST n_gamma; stats: HOST or NULL. 1 <= n_gamma <= 256. flags: LHAF_PLAIN_ACCUM,
+ *   LHAF_NO_REPEAT_SPEEDUP. Errors: LHAF_EINVAL for bad arguments (NULL, non-finite entries of the
+ *   occupied modes, negative reps, other flags), LHAF_ETOOBIG when ceil(N/2) > 24 (the staged series
+ *   limit) or the working dimension exceeds LHAF_MAX_DIM, LHAF_ECUDA / LHAF_ENOMEM as for lhaf(). The middle digits of even-eta pairs
  *   are evaluated on the full working matrix (no zero-digit groups). Synchronous. */
 lhaf_status lhaf_multi_gamma(lhaf_ctx* ctx, int M, const lhaf_c128* B, int n_gamma, const lhaf_c128* gammas,
                              const int32_t* reps, uint32_t flags, lhaf_c128* out, lhaf_stats* stats);
@@ -254,7 +255,9 @@ lhaf_status gbs_pattern_prob(lhaf_ctx* ctx, int M, const lhaf_c128* U, const dou
  * repeated-pair sieve of App. B.2 over pairs of equal counts: prod (n_i + 1) terms, halved). This
  * covers lossy states exactly, without a pure-state decomposition.
  *   sigma: HOST 2M x 2M row-major; alpha: HOST M or NULL; n: HOST M; prob: HOST;
- *   lhaf_A: HOST, optional (the loop hafnian of A_n). flags as for lhaf() (host pointers). */
+ *   lhaf_A: HOST, optional (the loop hafnian of A_n). flags as for lhaf() (host pointers; with
+ *   LHAF_ET the paper's lhafmix inclusion/exclusion form). Errors: LHAF_EINVAL for NULL, negative
+ *   counts, non-finite entries or a singular sigma_Q; otherwise those of lhaf(). */
 lhaf_status gbs_pattern_prob_mixed(lhaf_ctx* ctx, int M, const lhaf_c128* sigma, const lhaf_c128* alpha,
                                    const int32_t* n, uint32_t flags, double* prob, lhaf_c128* lhaf_A);
 
