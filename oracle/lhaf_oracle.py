@@ -10,7 +10,8 @@ Plain CPU restatement of the paper's formulas, written for checking by eye again
 * ``lhaf_fds_dense``   -- finite difference sieve on an explicit matrix (App. B.4, Eq. fdsieve).
 * ``matched_reps``     -- greedy choice of repeated pairs (App. B.3, steps 1-5).
 * ``lhaf_repeated``    -- finite difference sieve over repeated pairs (App. B.2 and the last
-  paragraph of App. B.4): per pair, delta runs from -eta to +eta in steps of 2.
+  paragraph of App. B.4): per pair, delta runs from -eta to +eta in steps of 2. Power traces by
+  repeated products, or from eigenvalues (App. B.1's route) on request.
 * ``lhaf_grad_minor``  -- d lhaf / d B and d lhaf / d gamma from the definition (a derivative of a
   matching sum is the matching sum of a minor).
 
@@ -122,6 +123,28 @@ def _g_coefficients(C: np.ndarray, v: np.ndarray, Xs: np.ndarray, h: int) -> np.
         P = np.matmul(P, CX)  # now (C X)^k
         tr = np.einsum("tii->t", P)
         g[:, k - 1] = tr / dt.type(2 * k) + loop / dt.type(2)
+    return g
+
+
+def _g_coefficients_eig(C: np.ndarray, v: np.ndarray, Xs: np.ndarray, h: int) -> np.ndarray:
+    """The same g_k with the traces taken from eigenvalues, the route App. B.1 names:
+    Tr((C X)^k) = sum_i lambda_i^k over the eigenvalues of C X (valid for any matrix, defective or
+    not); the loop terms v X (C X)^(k-1) v^T by repeated matrix-vector products."""
+    T, n, _ = Xs.shape
+    g = np.zeros((T, h), dtype=np.complex128)
+    if n == 0:
+        return g
+    CX = np.matmul(C[None, :, :], Xs)
+    lam = np.linalg.eigvals(CX)  # (T, n)
+    vX = np.matmul(v[None, None, :], Xs)[:, 0, :]  # (T, n)
+    w = np.broadcast_to(v, (T, n)).astype(np.complex128)  # (C X)^(k-1) v^T
+    power = np.ones_like(lam)
+    for k in range(1, h + 1):
+        power = power * lam
+        tr = power.sum(axis=1)
+        loop = np.einsum("ti,ti->t", vX, w)
+        w = np.einsum("tij,tj->ti", CX, w)
+        g[:, k - 1] = tr / (2 * k) + loop / 2
     return g
 
 
@@ -304,7 +327,7 @@ def reduced_slot_problem(B, gamma, reps):
 
 
 def repeated_sieve_terms(B, gamma, reps, start: int = 0, stop: Optional[int] = None,
-                         batch: int = 2048, dtype=np.complex128) -> list:
+                         batch: int = 2048, dtype=np.complex128, traces: str = "products") -> list:
     """The signed, weighted sieve terms prod_i C(eta_i,k_i) (-1)^(k_i) f(C X_delta') for the digit
     vectors k number start..stop-1 in itertools.product order (App. B.2, B.4). Used by
     lhaf_repeated (all terms) and by timing on a bounded sample of terms. dtype: complex128 (the
@@ -328,26 +351,30 @@ def repeated_sieve_terms(B, gamma, reps, start: int = 0, stop: Optional[int] = N
             ],
             dtype=float,
         ).astype(dtype)
-        g = _g_coefficients(C, v, _pairing_matrices(deltas, dtype), h)
+        if traces == "eigenvalues":
+            g = _g_coefficients_eig(C, v, _pairing_matrices(deltas), h)
+        else:
+            g = _g_coefficients(C, v, _pairing_matrices(deltas, dtype), h)
         f = et_poly_coefficient(g, h)
         terms.extend(list(weights * f))
     return terms
 
 
-def lhaf_repeated(B, gamma, reps, batch: int = 2048, dtype=np.complex128):
+def lhaf_repeated(B, gamma, reps, batch: int = 2048, dtype=np.complex128, traces: str = "products"):
     """lhaf(A_n) by the finite difference sieve over greedy repeated pairs (App. B.2, B.4).
 
     For pair i repeated eta_i times, k_i in 0..eta_i copies carry -1, so
     delta'_i = eta_i - 2 k_i with multiplicity C(eta_i, k_i) and sign (-1)^(k_i):
       lhaf = 2^(-h) sum_k prod_i C(eta_i,k_i) (-1)^(k_i) f(C X_delta'),  h = N/2,
     with f the lambda^h coefficient of Eq. ET_poly for the reduced slot matrix. Every digit
-    vector is summed (no halving).
+    vector is summed (no halving). traces="eigenvalues" takes the power traces from eigenvalues
+    (App. B.1) instead of repeated products (complex128 only).
     """
     N = int(sum(int(r) for r in reps))
     if N == 0:
         return 1.0 + 0j
     h = (N + 1) // 2
-    terms = repeated_sieve_terms(B, gamma, reps, batch=batch, dtype=dtype)
+    terms = repeated_sieve_terms(B, gamma, reps, batch=batch, dtype=dtype, traces=traces)
     if np.dtype(dtype) == np.complex128:
         return _fsum_complex(terms) / 2.0**h
     # extended precision: sum in that precision, smallest magnitudes first

@@ -51,6 +51,23 @@ def test_sieve_and_et_all_ones_give_involutions(n):
         assert lo.lhaf_et(J).real == pytest.approx(involutions(n), rel=1e-12)
 
 
+@pytest.mark.parametrize("n", range(1, 11))
+def test_eigenvalue_traces_all_ones_and_bruteforce(n):
+    # the eigenvalue route for the power traces (App. B.1): involutions on the all-ones matrix (its
+    # X-paired products are rank one, often nilpotent) and the brute-force sum on random matrices
+    ones = np.ones(n, dtype=np.int64)
+    J = np.ones((n, n))
+    assert lo.lhaf_repeated(J, np.ones(n), ones, traces="eigenvalues").real == pytest.approx(involutions(n), rel=1e-9)
+    rng = np.random.default_rng(77 + n)
+    A = rsym(rng, n)
+    got = lo.lhaf_repeated(A, np.diag(A).copy(), ones, traces="eigenvalues")
+    assert rel(got, lo.lhaf_bruteforce(A)) < 1e-10
+    reps = [int(x) for x in rng.integers(0, 3, size=4)]
+    B = rsym(rng, 4)
+    g = rsym(rng, 4).diagonal().copy()
+    assert rel(lo.lhaf_repeated(B, g, reps, traces="eigenvalues"), lo.lhaf_repeated(B, g, reps)) < 1e-10
+
+
 @pytest.mark.parametrize("m", range(1, 6))
 def test_hafnian_of_J_minus_I_is_double_factorial(m):
     A = np.ones((2 * m, 2 * m)) - np.eye(2 * m)  # no loops: perfect matchings only
