@@ -25,7 +25,7 @@ static thread_local char g_last_error[512] = "";
 int record_cuda(cudaError_t e, const char* what) {
   std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
   cudaGetLastError();  // clear a non-sticky error so it is not reported twice
-  return (lhaf_status)record_cuda(cudaPeekAtLastError(), "lhaf_api.cpp:28");
+  return LHAF_ECUDA;
 }
 void record_message(const char* msg) { std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
 }  // namespace lhafgpu
@@ -84,7 +84,7 @@ extern "C" lhaf_status lhaf_ctx_create(lhaf_ctx** out, int device, void* cuda_st
   c->device = device;
   if (cudaSetDevice(device) != cudaSuccess) {
     delete c;
-    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "lhaf_api.cpp:89");
+    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "cudaSetDevice");
   }
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
   if (cuda_stream) {
@@ -92,7 +92,7 @@ extern "C" lhaf_status lhaf_ctx_create(lhaf_ctx** out, int device, void* cuda_st
   } else {
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
       delete c;
-      return (lhaf_status)record_cuda(cudaPeekAtLastError(), "lhaf_api.cpp:97");
+      return (lhaf_status)record_cuda(cudaPeekAtLastError(), "cudaStreamCreate");
     }
     c->own_stream = true;
   }

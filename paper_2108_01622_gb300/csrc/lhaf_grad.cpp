@@ -57,7 +57,7 @@ extern "C" lhaf_status lhaf_grad(lhaf_ctx* ctx, int M, const lhaf_c128* B, const
   build_chat_host(pl, M, B, gamma, (std::complex<double>*)ctx->h_chat);
   if (cudaMemcpyAsync(ctx->d_chat, ctx->h_chat, sizeof(double2) * nd * nd, cudaMemcpyHostToDevice, ctx->stream) !=
       cudaSuccess)
-    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "lhaf_grad.cpp:60");
+    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "slot matrix upload");
   // team size: largest number of resident warps, preferring 16 or 32 lanes per term
   const size_t tb = grad_team_bytes(nd, pl.H, pl.h, pl.bord);
   const size_t ib = cta_table_bytes(false, pl.Hl, pl.H);
@@ -96,17 +96,17 @@ extern "C" lhaf_status lhaf_grad(lhaf_ctx* ctx, int M, const lhaf_c128* B, const
     return LHAF_ENOMEM;
   if (launch_grad(team, ctx->d_chat, p, (int)grid, ctx->d_partials, (double2*)ctx->b_gpart.p, ctx->stream) !=
       cudaSuccess)
-    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "lhaf_grad.cpp:99");
+    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "adjoint kernel");
   if (launch_reduce(ctx->d_partials, (long long)p.total_teams, pl.h, ctx->d_out, (double2*)(ctx->d_out + 4),
                     ctx->stream) != cudaSuccess)
-    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "lhaf_grad.cpp:102");
+    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "value reduction");
   if (launch_grad_reduce((const double2*)ctx->b_gpart.p, (long long)p.total_teams, len, pl.h, (double2*)ctx->b_gout.p,
                          ctx->stream) != cudaSuccess)
-    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "lhaf_grad.cpp:105");
+    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "gradient reduction");
   if (cudaMemcpyAsync(ctx->h_out, ctx->d_out, 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
       cudaMemcpyAsync(ctx->hb_gout.p, ctx->b_gout.p, sizeof(double2) * len, cudaMemcpyDeviceToHost, ctx->stream) !=
           cudaSuccess)
-    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "lhaf_grad.cpp:109");
+    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "result copy");
   if (const cudaError_t e_ = (cudaStreamSynchronize(ctx->stream)); e_ != cudaSuccess) return (lhaf_status)record_cuda(e_, "cudaStreamSynchronize");
   *value = {ctx->h_out[4], ctx->h_out[5]};
   const std::complex<double>* g = static_cast<const std::complex<double>*>(ctx->hb_gout.p);
