@@ -432,3 +432,82 @@ def test_mixed_planted_mistakes_are_caught(mutation, monkeypatch):
 
     monkeypatch.setattr(go, "gbs_kernel", kernel)
     assert not _mixed_pins_pass()
+
+
+# ---------------------------------------------------------------------------------------------
+# The oracle's extended-precision mode (dtype=np.clongdouble), the reference of the most
+# ill-conditioned GPU parity cases: exact closed forms, and the definition in 50-digit mpmath.
+# ---------------------------------------------------------------------------------------------
+
+
+def _ld_to_mp(mpmath, x):
+    """An extended-precision real as an mpmath number, exactly (two doubles hold its mantissa)."""
+    hi = float(x)
+    return mpmath.mpf(hi) + mpmath.mpf(float(x - np.longdouble(hi)))
+
+
+@pytest.mark.parametrize("kind,n", [("involutions", 9), ("involutions", 12), ("double_factorial", 10),
+                                    ("double_factorial", 14), ("permanent", 6), ("permanent", 8)])
+def test_extended_precision_closed_forms(kind, n):
+    # one mode repeated n times with B = gamma = 1 is J_n (involution numbers); with gamma = 0 it
+    # is the hafnian of J_n - I ((n - 1)!!); two modes coupled only to each other, n photons
+    # each, give the bipartite block [[0, J_n], [J_n, 0]] (perm J_n = n!)
+    if kind == "involutions":
+        B, g, reps, want = np.ones((1, 1), complex), np.ones(1, complex), (n,), involutions(n)
+    elif kind == "double_factorial":
+        B, g, reps, want = np.ones((1, 1), complex), np.zeros(1, complex), (n,), math.prod(range(n - 1, 0, -2))
+    else:
+        B = np.array([[0, 1], [1, 0]], complex)
+        g, reps, want = np.zeros(2, complex), (n, n), math.factorial(n)
+    got = lo.lhaf_repeated(B, g, reps, dtype=np.clongdouble)
+    assert isinstance(got, np.clongdouble)
+    assert abs(np.real(got) - np.longdouble(want)) <= 64 * np.finfo(np.longdouble).eps * want
+    assert abs(np.imag(got)) <= 64 * np.finfo(np.longdouble).eps * want
+
+
+def test_extended_precision_beats_complex128_against_mpmath_definition():
+    # Repeated patterns with N <= 12 and counts 4..6: the sieve's signed sum cancels (sum |terms|
+    # / |lhaf| up to ~70). The definition (brute-force matching sum of the expanded matrix in
+    # 50-digit mpmath) is the truth for the same inputs. The extended-precision sieve must land
+    # at least 100x closer to it than the complex128 sieve (summed over the instances), and
+    # below 1e-17 relative on average; a silent downcast to complex128 anywhere in the dtype
+    # plumbing makes the two errors equal and fails both.
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    from paper_2108_01622_gb300 import workloads as wl
+
+    err128, err_ld = [], []
+    for reps in [(4, 4, 4), (5, 5, 2), (6, 4, 2), (4, 4, 2, 2), (6, 6)]:
+        for seed in range(3):
+            p = wl.small_problem(seed=seed, M=len(reps), reps=reps, loops=True)
+            A = lo.expand_pattern(p.B, p.gamma, p.reps)
+            N = len(A)
+            ref = lo.lhaf_bruteforce([[mpmath.mpc(complex(A[i, j])) for j in range(N)] for i in range(N)])
+            d = lo.lhaf_repeated(p.B, p.gamma, p.reps)
+            e = lo.lhaf_repeated(p.B, p.gamma, p.reps, dtype=np.clongdouble)
+            err128.append(float(abs(mpmath.mpc(complex(d)) - ref) / abs(ref)))
+            e_mp = mpmath.mpc(_ld_to_mp(mpmath, np.real(e)), _ld_to_mp(mpmath, np.imag(e)))
+            err_ld.append(float(abs(e_mp - ref) / abs(ref)))
+    assert max(err128) < 1e-13  # the complex128 sieve itself is right
+    assert sum(err_ld) / len(err_ld) < 1e-17
+    assert sum(err128) >= 100 * sum(err_ld)
+
+
+@pytest.mark.parametrize("where", ["terms", "coefficients", "series"])
+def test_extended_precision_downcast_is_caught(where, monkeypatch):
+    # plant a silent complex128 round trip at one step of the extended-precision plumbing
+    def down(a):
+        return np.asarray(a).astype(np.complex128).astype(np.asarray(a).dtype)
+
+    if where == "terms":
+        orig_t = lo.repeated_sieve_terms
+        monkeypatch.setattr(lo, "repeated_sieve_terms",
+                            lambda *a, **k: [down(np.asarray([t]))[0] for t in orig_t(*a, **k)])
+    elif where == "coefficients":
+        orig_g = lo._g_coefficients
+        monkeypatch.setattr(lo, "_g_coefficients", lambda C, v, Xs, h: down(orig_g(C, v, Xs, h)))
+    else:
+        orig_e = lo.et_poly_coefficient
+        monkeypatch.setattr(lo, "et_poly_coefficient", lambda g, h: down(orig_e(down(g), h)))
+    with pytest.raises(AssertionError):
+        test_extended_precision_beats_complex128_against_mpmath_definition()
