@@ -101,7 +101,7 @@ typedef struct {
   uint64_t h2d_bytes;   /* bytes this call copied host -> device (inputs, descriptors) */
   uint64_t d2h_bytes;   /* bytes this call copied device -> host (results) */
   int32_t launches;     /* CUDA kernels this call launched (tuning trials excluded) */
-  int32_t reserved;
+  int32_t term_launches; /* of those, launches of the sieve-term kernel (each bounded: see lhaf) */
 } lhaf_stats;
 
 /* Create a context on `device`. cuda_stream: a cudaStream_t to order work on (cudaStreamLegacy or
@@ -132,7 +132,13 @@ lhaf_status lhaf_plan(int M, const int32_t* reps, uint32_t flags, int has_loops,
                       int32_t* n_dim, int32_t* h, int32_t* pairs);
 
 /* lhaf(B_n) (App. B.4 Eq. fdsieve with the repeated pairs of App. B.2-B.4).
- * out: one lhaf_c128 (host, or device with LHAF_DEVICE_PTRS). stats: host pointer or NULL. */
+ * out: one lhaf_c128 (host, or device with LHAF_DEVICE_PTRS). stats: host pointer or NULL.
+ * Launches are bounded: degrees up to 24 run in launches sized to a 256 MB staging buffer; above
+ * that (series finished inside the team) every launch of the sieve-term kernel covers at most
+ * 2.5e11 model flops (about a quarter second on GB300; the environment variable
+ * LHAF_LAUNCH_MFLOPS overrides, in millions), and its per-term partials are reduced in term order,
+ * so a long sum holds the GPU in short launches and the same range gives the same bits whichever
+ * CTA took which terms (for a given team size). */
 lhaf_status lhaf(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128* gamma,
                  const int32_t* reps, uint32_t flags, lhaf_c128* out, lhaf_stats* stats);
 

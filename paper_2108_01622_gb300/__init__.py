@@ -45,7 +45,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("terms", ctypes.c_uint64), ("n_dim", ctypes.c_int32), ("h", ctypes.c_int32),
                 ("pairs", ctypes.c_int32), ("team", ctypes.c_int32), ("kernel_ms", ctypes.c_double),
                 ("flops_model", ctypes.c_double), ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
-                ("launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("launches", ctypes.c_int32), ("term_launches", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

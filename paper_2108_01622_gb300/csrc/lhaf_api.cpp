@@ -381,6 +381,19 @@ lhaf_status validate_host_inputs(int M, const lhaf_c128* B, const lhaf_c128* gam
 // Staging buffer for the series kernel: grown on demand (terms x coefficient rows).
 constexpr size_t kStageBytesMax = (size_t)256 << 20;
 
+// Unstaged launches (series finished inside the team, h > kStageMaxDegree): each launch covers at
+// most kLaunchModelFlops of model work (about 0.25 s at GB300's FP64 rate; LHAF_LAUNCH_MFLOPS
+// overrides, in millions) and at most kMaxChunkParts term slots, whose per-chunk partials are
+// reduced in chunk order, so that a launch's sum does not depend on which CTA took which chunk.
+constexpr double kLaunchModelFlops = 2.5e11;
+constexpr uint64_t kMaxChunkParts = (uint64_t)1 << 21;
+
+double launch_flops_budget() {
+  const char* env = std::getenv("LHAF_LAUNCH_MFLOPS");
+  const double v = env ? std::atof(env) * 1e6 : 0.0;
+  return v > 0.0 ? v : kLaunchModelFlops;
+}
+
 }  // namespace
 
 bool lhafgpu::ensure_stage(lhaf_ctx* ctx, size_t bytes, size_t terms) {
@@ -503,7 +516,7 @@ lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& 
       return (lhaf_status)record_cuda(cudaPeekAtLastError(), "eigenvalue-trace rank table");
   }
   uint64_t h2d = sizeof(BatchItem) * (uint64_t)nj + et_bytes;
-  int launches = 0;
+  int launches = 0, term_launches = 0;
   if (cudaMemcpyAsync(w.items.p, jobs, sizeof(BatchItem) * nj, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return (lhaf_status)record_cuda(cudaPeekAtLastError(), "group descriptors");
   if (dev) {
@@ -621,7 +634,21 @@ lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& 
     const bool last_class = cl + 1 == classes.size();
     if (lc.c1 <= lc.c0 && !(first && last_class)) continue;  // nothing of the range in this class
     first = false;
-    const long long span = staged ? std::max<long long>(1, (long long)(cap_cols / lc.tpc)) : (lc.c1 - lc.c0);
+    long long span = 1;
+    if (staged) {
+      span = std::max<long long>(1, (long long)(cap_cols / lc.tpc));
+    } else {
+      // bounded launches: the class's costliest sieve sets the terms per launch
+      double fpt = 1.0;
+      for (int j = lc.j0; j < lc.j1; j++) {
+        const Plan& sj = subs[order[j]];
+        fpt = std::max(fpt, lhaf_model_flops_per_term(sj.nd, sj.h, sj.bord));
+      }
+      const double terms = std::max(1.0, launch_flops_budget() / fpt);
+      span = std::max<long long>(1, (long long)std::min<double>(terms / lc.tpc, (double)(kMaxChunkParts / lc.tpc)));
+      span = std::min<long long>(span, std::max<long long>(1, lc.c1 - lc.c0));
+      if (!w.parts.reserve(sizeof(double) * 4 * (size_t)span * (size_t)lc.tpc)) return LHAF_ENOMEM;
+    }
     const uint64_t max_ctas = (uint64_t)ctx->sms * (uint64_t)lc.occ;
     long long c0 = lc.c0;
     do {
@@ -631,17 +658,18 @@ lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& 
       if (n > 0) {
         unsigned long long rounds = 1;
         const uint64_t grid = balanced_grid((uint64_t)n, 1, max_ctas, &rounds);
-        if (!staged && grid * (uint64_t)lc.tpc > ctx->partial_cap) return LHAF_ETOOBIG;
         if (cudaMemsetAsync(w.counter.p, 0, sizeof(unsigned long long), s) != cudaSuccess)
           return (lhaf_status)record_cuda(cudaPeekAtLastError(), "chunk queue reset");
         cudaError_t e = launch_grouped_terms(fp32, lc.team, pool_ptr, (const BatchItem*)w.items.p, nj,
                                              (const long long*)w.chunks.p, c0, c1, (int)grid, (int)rounds, tb, te,
-                                             (int)lc.team_bytes, (int)lc.items_bytes, ctx->d_partials,
+                                             (int)lc.team_bytes, (int)lc.items_bytes,
+                                             staged ? ctx->d_partials : static_cast<double*>(w.parts.p),
                                              staged ? ctx->d_stage : nullptr, staged ? ctx->d_wstage : nullptr,
-                                             staged ? (long long)cap_cols : 0, s, 0,
+                                             staged ? (long long)cap_cols : 0, s, staged ? 0 : 1,
                                              (unsigned long long*)w.counter.p);
         if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "grouped terms kernel");
         launches++;
+        term_launches++;
         if (staged) {
           e = launch_series(fp32, ctx->d_stage, ctx->d_wstage, n * lc.tpc, (long long)cap_cols, pl.h, pl.bord,
                             (flags & LHAF_PLAIN_ACCUM) ? 1 : 0, ctx->d_partials, s);
@@ -649,7 +677,7 @@ lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& 
           launches++;
           nparts = series_blocks(n * lc.tpc);
         } else {
-          nparts = (long long)grid * lc.tpc;
+          nparts = n * lc.tpc;  // one partial per chunk term slot, in chunk order
         }
       }
       bool last = last_class && c1 >= lc.c1;
@@ -658,8 +686,8 @@ lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& 
         for (size_t k2 = cl + 1; k2 < classes.size(); k2++)
           if (classes[k2].c1 > classes[k2].c0) last = false;
       }
-      cudaError_t e =
-          launch_reduce(ctx->d_partials, nparts, pl.h, acc_dd, last ? val_dst : nullptr, s, ci > 0 ? 1 : 0);
+      cudaError_t e = launch_reduce(staged ? ctx->d_partials : static_cast<double*>(w.parts.p), nparts, pl.h, acc_dd,
+                                    last ? val_dst : nullptr, s, ci > 0 ? 1 : 0);
       if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "reduction kernel");
       launches++;
       c0 = c1;
@@ -683,6 +711,7 @@ lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& 
     stats->flops_model = flops;
     stats->kernel_ms = 0.0;
     stats->launches = launches;
+    stats->term_launches = term_launches;
     stats->h2d_bytes = h2d;
   }
   return LHAF_OK;

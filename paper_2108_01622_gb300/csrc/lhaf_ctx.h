@@ -70,6 +70,7 @@ struct BatchWork {
   DevBuf item_h, acc, entries, chat, chat32, out, stage, wstage, in_B, in_gamma;
   DevBuf counter;    // chunk queue of a grouped launch (zeroed before each launch)
   DevBuf et_table;   // eigenvalue-trace rank table of one loop hafnian
+  DevBuf parts;      // per-chunk dd partials of an unstaged launch (4 doubles per chunk term slot)
   HostBuf h_et_table;
   HostBuf h_items, h_chunks, h_seg_begin, h_seg_item, h_item_h, h_chat, h_chat32, h_out, h_in;
   cudaEvent_t uploaded = nullptr;  // after the last copies that read the pinned buffers above
@@ -77,7 +78,7 @@ struct BatchWork {
     if (uploaded) cudaEventDestroy(uploaded);
     uploaded = nullptr;
     for (DevBuf* b : {&items, &chunks, &seg_begin, &seg_item, &item_h, &acc, &entries, &chat, &chat32, &out, &stage,
-                      &wstage, &in_B, &in_gamma, &counter, &et_table})
+                      &wstage, &in_B, &in_gamma, &counter, &et_table, &parts})
       b->release();
     for (HostBuf* b : {&h_et_table, &h_items, &h_chunks, &h_seg_begin, &h_seg_item, &h_item_h, &h_chat, &h_chat32, &h_out, &h_in})
       b->release();

@@ -1163,7 +1163,13 @@ grouped_terms_kernel(const typename Cx<R>::t* __restrict__ chat_pool, const Batc
     __syncthreads();
     const bool valid_desc = sp.nd >= 2 && sp.nd <= kMaxDim && sp.P <= kMaxPairs && sp.h <= kMaxDegree &&
                             sp.Hl <= sp.nd && sp.n_items == sp.Hl * (sp.Hl - 1) / 2;
-    if (!valid_desc) continue;  // a description outside the compiled limits is skipped
+    if (!valid_desc) {  // a description outside the compiled limits is skipped (its slots read 0)
+      if (!STAGE && per_chunk && lt == 0) {
+        double* o = partials + 4ll * ((k - k_begin) * TEAMS + team);
+        o[0] = o[1] = o[2] = o[3] = 0.0;
+      }
+      continue;
+    }
     if (j != s_job || sp.Hl != s_Hl) {
       build_cta_tables<R, CTA>(sp, smem);
       __syncthreads();

@@ -71,14 +71,16 @@ def _device_for(dist, group):
 
 
 def gather_partials(part, group=None) -> np.ndarray:
-    """All-gather of one 4-double partial per rank -> world x 4 array (rank order)."""
+    """All-gather of n 4-double partials per rank (the same n on every rank) -> (world * n) x 4
+    array in rank order (so in term order when each rank's partials are in term order)."""
     import torch
 
     dist, _, world = _dist(group)
-    t = torch.as_tensor(np.asarray(part, dtype=np.float64).reshape(4)).to(_device_for(dist, group))
+    t = torch.as_tensor(np.ascontiguousarray(np.asarray(part, dtype=np.float64).reshape(-1, 4)))
+    t = t.to(_device_for(dist, group))
     outs = [torch.empty_like(t) for _ in range(world)]
     dist.all_gather(outs, t, group=group)
-    return np.stack([o.cpu().numpy() for o in outs])
+    return np.concatenate([o.cpu().numpy() for o in outs], axis=0)
 
 
 def lhaf_sharded(ctx, B, gamma=None, reps=None, flags: int = 0, group=None) -> complex:
