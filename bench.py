@@ -83,75 +83,53 @@ def survey_flops_per_term(n: int, h: int) -> float:
 
 # ------------------------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline and the reference arm): the oracle as it stands, on a bounded
-# sample of the same workload's sieve terms, spread over the host cores with a spawn pool.
-# The oracle sums every digit vector; its first half (first digit below the middle) is the half
-# the library evaluates, term for term of the same cost, so its terms/s is in the same units and
-# ms per lhaf = (evaluated terms) / rate.
+# sample of the same workload's sieve terms, over the host cores. The oracle sums every digit
+# vector; its first half (first digit below the middle) is the half the library evaluates, term
+# for term of the same cost, so its terms/s is in the same units and ms per lhaf = (evaluated
+# terms) / rate.
 # ------------------------------------------------------------------------------------------
 
 
-def _oracle_slice(args):
-    workload, start, stop = args
-    sys.path.insert(0, ROOT)
-    from oracle import lhaf_oracle as lo
-
-    p = load_problem(workload)
-    t0 = time.perf_counter()
-    terms = lo.repeated_sieve_terms(p.B, p.gamma, p.reps, start, stop)
-    return len(terms), time.perf_counter() - t0
-
-
 class OracleTimer:
-    """The oracle as it stands, timed on slices of the workload's sieve terms over all host cores
-    (one spawn pool, created before any GPU call)."""
+    """The C oracle as it stands (Householder Hessenberg form, La Budde's recurrence, Newton's
+    identities; OpenMP over terms on every host core), timed on slices of the workload's sieve
+    terms."""
 
     def __init__(self, workload: str):
-        import multiprocessing as mp
-
+        from oracle import csieve
         from oracle import lhaf_oracle as lo
 
-        self.workload = workload
-        p = load_problem(workload)
-        self.total_terms = lo.repeated_term_count(p.reps)
+        self.cs = csieve
+        self.p = load_problem(workload)
+        self.total_terms = lo.repeated_term_count(self.p.reps)
         self.half = max(1, self.total_terms // 2)
-        self.cores = os.cpu_count() or 1
-        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
-        for k in saved:  # one BLAS thread per worker process: `cores` is the number of processes
-            os.environ[k] = "1"
-        self.pool = mp.get_context("spawn").Pool(self.cores)
-        for k, v in saved.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
-        warm = 16 if workload == "large60" else 64
-        self.pool.map(_oracle_slice, [(workload, 0, warm)] * self.cores)  # workers import numpy, warm up
-        n, dt = _oracle_slice((workload, 0, 4 * warm))
-        self.per_term = dt / max(n, 1)
-        self.cursor = 4 * warm
+        _, self.cores = csieve.sieve_sum(self.p.B, self.p.gamma, self.p.reps, 0, 64)  # builds, warms up
+        n = min(self.half, 16 * self.cores)
+        t0 = time.perf_counter()
+        csieve.sieve_sum(self.p.B, self.p.gamma, self.p.reps, 0, n)
+        self.per_term = (time.perf_counter() - t0) / n
+        self.cursor = n
 
     def sample(self, seconds: float, evaluated_terms: int):
-        per_worker = max(8, int(seconds / self.per_term))
-        chunks = []
-        for _ in range(self.cores):
-            if self.cursor + per_worker > self.half:
-                self.cursor = 0
-            chunks.append((self.workload, self.cursor, self.cursor + per_worker))
-            self.cursor += per_worker
+        n = max(4 * self.cores, int(seconds / self.per_term))
+        n = min(n, self.half)
+        if self.cursor + n > self.half:
+            self.cursor = 0
         t0 = time.perf_counter()
-        res = self.pool.map(_oracle_slice, chunks)
+        _, used = self.cs.sieve_sum(self.p.B, self.p.gamma, self.p.reps, self.cursor, self.cursor + n)
         wall = time.perf_counter() - t0
-        done = sum(r[0] for r in res)
-        rate = done / wall
-        return {"value": rate, "unit": UNIT, "cores": self.cores, "kind": "oracle",
-                "sample": (f"{done} sieve terms of the same workload (slices of the half the library evaluates, "
-                           f"{self.total_terms} digit vectors in all), numpy oracle, {self.cores}-process spawn pool, "
+        self.cursor += n
+        self.per_term = wall / n
+        rate = n / wall
+        return {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
+                "sample": (f"{n} sieve terms of the same workload (a contiguous slice of the half the library "
+                           f"evaluates; {self.total_terms} digit vectors in all), C oracle (Householder Hessenberg, "
+                           f"La Budde, Newton; FP64, long-double sums), OpenMP over terms on {used} threads, "
                            f"{wall:.1f} s wall"),
                 "ms_per_lhaf": evaluated_terms / rate * 1e3}
 
     def close(self):
-        self.pool.close()
-        self.pool.join()
+        pass
 
 
 # ------------------------------------------------------------------------------------------
@@ -271,7 +249,7 @@ def run_ours(args, rank, world, local_rank):
 
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        timer = OracleTimer(args.workload)  # spawn pool started before the first GPU call
+        timer = OracleTimer(args.workload)  # before the first GPU call
         cpu_base = timer.sample(15.0, T_all)
         timer.close()
 

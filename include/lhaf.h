@@ -56,7 +56,10 @@ typedef enum {
 /* Flags (bitwise OR). */
 #define LHAF_DEVICE_PTRS 0x1u        /* B, gamma and outputs are device pointers, stream-ordered */
 #define LHAF_FP32_TERMS 0x2u         /* per-term arithmetic in FP32 (accumulation stays in
-                                        double-double); error is larger, see the tests */
+                                        double-double), offered up to degree h = 18 (N <= 36
+                                        photons) with a stated bound of 1e-2 relative error
+                                        against FP64 (measured <= 1.2e-3 there; 2.7e-2 at
+                                        N = 60): larger problems give LHAF_ETOOBIG */
 #define LHAF_PLAIN_ACCUM 0x4u        /* accumulate the signed sum in plain FP64 instead of
                                         double-double (for accuracy comparisons) */
 #define LHAF_NO_REPEAT_SPEEDUP 0x8u  /* pair photons one by one (all eta = 1): the sieve of the
@@ -133,12 +136,12 @@ lhaf_status lhaf_plan(int M, const int32_t* reps, uint32_t flags, int has_loops,
 
 /* lhaf(B_n) (App. B.4 Eq. fdsieve with the repeated pairs of App. B.2-B.4).
  * out: one lhaf_c128 (host, or device with LHAF_DEVICE_PTRS). stats: host pointer or NULL.
- * Launches are bounded: degrees up to 24 run in launches sized to a 256 MB staging buffer; above
- * that (series finished inside the team) every launch of the sieve-term kernel covers at most
- * 2.5e11 model flops (about a quarter second on GB300; the environment variable
- * LHAF_LAUNCH_MFLOPS overrides, in millions), and its per-term partials are reduced in term order,
- * so a long sum holds the GPU in short launches and the same range gives the same bits whichever
- * CTA took which terms (for a given team size). */
+ * Launches are bounded: every launch of the sieve-term kernel covers at most 2.5e11 model flops
+ * (about a quarter second on GB300; the environment variable LHAF_LAUNCH_MFLOPS overrides, in
+ * millions). Degrees up to 32 stage their term polynomials (at most 256 MB per launch) and finish
+ * them one term per thread; above that the series is finished inside the team and the launch's
+ * per-term partials are reduced in term order. So a long sum holds the GPU in short launches, and
+ * the same range gives the same bits whichever CTA took which terms (for a given team size). */
 lhaf_status lhaf(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128* gamma,
                  const int32_t* reps, uint32_t flags, lhaf_c128* out, lhaf_stats* stats);
 
@@ -306,9 +309,10 @@ lhaf_status lhaf_combine(int count, const double* partials_dd, int32_t h, lhaf_c
  * Scratch: a fixed 224 KiB device array inside the library (slot matrix for working dimension
  * <= LHAF_MAX_DIM plus partial sums of at most 4096 GPU teams), held by every GPU that loads the
  * library until the process exits. Larger problems are rejected with LHAF_ETOOBIG; the number of
- * terms is not limited (teams loop over more terms). The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress) and caches it, so make that first call before any
- * stream capture. All calls share the one array and it keeps the last call's contents (nothing in
+ * terms is not limited (teams loop over more terms). Every call made outside stream capture looks
+ * up the array's device address (cudaGetSymbolAddress, so the address is found again after
+ * cudaDeviceReset) and caches it per device; a call made while its stream is capturing uses the
+ * cached address, so make the first call on each device before any stream capture. All calls share the one array and it keeps the last call's contents (nothing in
  * it needs to start at zero): calls that overlap on the GPU, e.g. on two streams, race and give
  * wrong results; order them on one stream or synchronise between them. */
 lhaf_status lhaf_noalloc(int device, void* cuda_stream, int M, const lhaf_c128* B, const lhaf_c128* gamma,

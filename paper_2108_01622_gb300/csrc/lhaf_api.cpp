@@ -381,10 +381,11 @@ lhaf_status validate_host_inputs(int M, const lhaf_c128* B, const lhaf_c128* gam
 // Staging buffer for the series kernel: grown on demand (terms x coefficient rows).
 constexpr size_t kStageBytesMax = (size_t)256 << 20;
 
-// Unstaged launches (series finished inside the team, h > kStageMaxDegree): each launch covers at
-// most kLaunchModelFlops of model work (about 0.25 s at GB300's FP64 rate; LHAF_LAUNCH_MFLOPS
-// overrides, in millions) and at most kMaxChunkParts term slots, whose per-chunk partials are
-// reduced in chunk order, so that a launch's sum does not depend on which CTA took which chunk.
+// Every launch of the sieve-term kernel covers at most kLaunchModelFlops of model work (about 0.25 s
+// at GB300's FP64 rate; LHAF_LAUNCH_MFLOPS overrides, in millions). Unstaged launches (series
+// finished inside the team, h > kStageMaxDegreeSingle) also hold at most kMaxChunkParts term
+// slots, whose per-chunk partials are reduced in chunk order, so that a launch's sum does not
+// depend on which CTA took which chunk (staged launches write their terms by column already).
 constexpr double kLaunchModelFlops = 2.5e11;
 constexpr uint64_t kMaxChunkParts = (uint64_t)1 << 21;
 
@@ -419,7 +420,7 @@ namespace {
 
 // One loop hafnian over its zero-digit groups `subs` (numbered group after group), restricted to
 // [tb, te): grid-strided chunks that never straddle two groups (grouped_terms_kernel), then, for
-// degrees up to kStageMaxDegree, the staged series one term per thread; both in launches sized to
+// degrees up to kStageMaxDegreeSingle, the staged series one term per thread; both in launches sized to
 // the staging buffer. Writes the unscaled dd partial to dd_dst and/or the value to val_dst.
 lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& subs, int M, const lhaf_c128* B,
                         const lhaf_c128* gamma, uint32_t flags, bool dev, uint64_t tb, uint64_t te, double* dd_dst,
@@ -427,7 +428,7 @@ lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& 
                         const std::vector<unsigned long long>* et_tab = nullptr) {
   const bool fp32 = (flags & LHAF_FP32_TERMS) != 0;
   const char* env_stage = std::getenv("LHAF_STAGE");
-  bool staged = pl.h <= kStageMaxDegree && !(env_stage && env_stage[0] == '0');
+  bool staged = pl.h <= kStageMaxDegreeSingle && !(env_stage && env_stage[0] == '0');
   const size_t cs = fp32 ? sizeof(float2) : sizeof(double2);
   const int rows = pl.bord ? 2 * pl.h + 1 : pl.h;
   BatchWork& w = ctx->gw;
@@ -634,18 +635,19 @@ lhaf_status run_grouped(lhaf_ctx* ctx, const Plan& pl, const std::vector<Plan>& 
     const bool last_class = cl + 1 == classes.size();
     if (lc.c1 <= lc.c0 && !(first && last_class)) continue;  // nothing of the range in this class
     first = false;
+    // bounded launches: the class's costliest sieve sets the terms per launch (flop budget), and
+    // the staging buffer (staged) or the per-chunk partial slots (inline series) cap it
+    double fpt = 1.0;
+    for (int j = lc.j0; j < lc.j1; j++) {
+      const Plan& sj = subs[order[j]];
+      fpt = std::max(fpt, lhaf_model_flops_per_term(sj.nd, sj.h, sj.bord));
+    }
+    const double budget_chunks = std::max(1.0, launch_flops_budget() / fpt / lc.tpc);
     long long span = 1;
     if (staged) {
-      span = std::max<long long>(1, (long long)(cap_cols / lc.tpc));
+      span = std::max<long long>(1, (long long)std::min<double>((double)(cap_cols / lc.tpc), budget_chunks));
     } else {
-      // bounded launches: the class's costliest sieve sets the terms per launch
-      double fpt = 1.0;
-      for (int j = lc.j0; j < lc.j1; j++) {
-        const Plan& sj = subs[order[j]];
-        fpt = std::max(fpt, lhaf_model_flops_per_term(sj.nd, sj.h, sj.bord));
-      }
-      const double terms = std::max(1.0, launch_flops_budget() / fpt);
-      span = std::max<long long>(1, (long long)std::min<double>(terms / lc.tpc, (double)(kMaxChunkParts / lc.tpc)));
+      span = std::max<long long>(1, (long long)std::min<double>(budget_chunks, (double)(kMaxChunkParts / lc.tpc)));
       span = std::min<long long>(span, std::max<long long>(1, lc.c1 - lc.c0));
       if (!w.parts.reserve(sizeof(double) * 4 * (size_t)span * (size_t)lc.tpc)) return LHAF_ENOMEM;
     }
@@ -739,6 +741,7 @@ lhaf_status lhaf_common(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c12
   bool loops = !(flags & LHAF_NO_LOOPS);
   lhaf_status st = build_plan(M, reps, flags, loops, pl);
   if (st != LHAF_OK) return st;
+  if ((flags & LHAF_FP32_TERMS) && pl.h > kFp32MaxDegree) return LHAF_ETOOBIG;  // beyond its stated bound
   if (!dev && loops && pl.N > 0 && !has_loops_host(pl, M, B, gamma)) {
     st = build_plan(M, reps, flags, false, pl);
     if (st != LHAF_OK) return st;

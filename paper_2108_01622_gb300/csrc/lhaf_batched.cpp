@@ -141,6 +141,7 @@ lhaf_status prepare_batch(lhaf_ctx* ctx, BatchWork& w, int batch, int M, const l
       }
       if (!any) st[i] = build_plan(M, r, flags, false, plans[i]);
     }
+    if (st[i] == LHAF_OK && fp32 && plans[i].h > kFp32MaxDegree) st[i] = LHAF_ETOOBIG;  // FP32 beyond its bound
     item_h[i] = st[i] != LHAF_OK ? INT_MAX : (plans[i].N == 0 ? -1 : plans[i].h);
   }
 

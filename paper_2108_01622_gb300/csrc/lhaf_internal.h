@@ -124,6 +124,15 @@ int max_ctas_per_sm(bool fp32, int team, size_t smem_bytes, bool staged = false)
 
 // Staged series: count terms (one per thread), partials: 4 doubles per block.
 constexpr int kStageMaxDegree = 24;
+// One loop hafnian (lhaf, lhaf_range) stages its term polynomials up to this degree: the series
+// then runs one term per thread instead of on a warp with shuffle reductions (series_kernel keeps
+// (4h + 5) x 64 complex values in shared memory: 136 KB at h = 32).
+constexpr int kStageMaxDegreeSingle = 32;
+// FP32 per-term arithmetic is offered up to this degree (N <= 36 photons), where its stated error
+// bound (1e-2 relative against FP64) holds with margin: measured on GB300 at most 1.2e-3 on
+// GBS-shaped and block-diagonal instances up to N = 36, but up to 7.6e-2 at N = 42 and 2.7e-2 at
+// N = 60. Larger problems with LHAF_FP32_TERMS are refused with LHAF_ETOOBIG.
+constexpr int kFp32MaxDegree = 18;
 size_t series_shared_bytes(bool fp32, int h);
 long long series_blocks(long long count);
 cudaError_t launch_series(bool fp32, const void* stage, const double* wstage, long long count,

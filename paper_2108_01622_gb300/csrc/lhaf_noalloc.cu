@@ -22,6 +22,7 @@
 #include "../../include/lhaf.h"
 #include "lhaf_internal.h"
 #include "lhaf_plan.h"
+#include "lhaf_ctx.h"
 
 namespace {
 
@@ -41,12 +42,19 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on `device` (which must be current). Resolved on the first
-// call per device and cached.
-lhaf_status scratch_address(int device, unsigned char** out) {
+// Device address of the scratch array on `device` (which must be current). Looked up with
+// cudaGetSymbolAddress on every call made outside stream capture (so a module reloaded after
+// cudaDeviceReset is found again) and cached per device; a call made while `stream` is capturing
+// uses the cached address (the first call on a device should come before any capture).
+lhaf_status scratch_address(int device, cudaStream_t stream, unsigned char** out) {
   if (device < 0 || device >= kMaxDevices) return LHAF_EINVAL;
   std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch_addr[device]) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    cs = cudaStreamCaptureStatusActive;  // cannot tell: do not touch the module state
+  }
+  if (cs == cudaStreamCaptureStatusNone || !g_scratch_addr[device]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
@@ -108,6 +116,7 @@ extern "C" lhaf_status lhaf_noalloc(int device, void* cuda_stream, int M, const 
   lhaf_status st = build_plan(M, reps, flags, loops, pl);
   if (st != LHAF_OK) return st;  // includes LHAF_ETOOBIG for n_dim > 64 (the slot-matrix limit)
   if (pl.nd > kMaxDim) return LHAF_ETOOBIG;
+  if (fp32 && pl.h > kFp32MaxDegree) return LHAF_ETOOBIG;  // FP32 terms beyond their stated bound
 
   if (pl.N == 0) {  // lhaf of the empty pattern is 1
     write_one<<<1, 1, 0, stream>>>((double2*)out);
@@ -115,7 +124,7 @@ extern "C" lhaf_status lhaf_noalloc(int device, void* cuda_stream, int M, const 
   }
 
   unsigned char* base = nullptr;
-  st = scratch_address(device, &base);
+  st = scratch_address(device, stream, &base);
   if (st != LHAF_OK) return st;
   double2* chat = reinterpret_cast<double2*>(base);
   float2* chat32 = reinterpret_cast<float2*>(base + kChatBytes);
@@ -128,29 +137,7 @@ extern "C" lhaf_status lhaf_noalloc(int device, void* cuda_stream, int M, const 
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return LHAF_ECUDA;
 
   TermParams p;
-  std::memset(&p, 0, sizeof(p));
-  p.nd = pl.nd;
-  p.ld = pl.nd | 1;
-  p.bord = pl.bord;
-  p.h = pl.h;
-  p.H = pl.H;
-  p.Hl = pl.Hl;
-  p.P = pl.P;
-  p.hp = pl.hp;
-  p.hp_even = pl.hp_even;
-  p.plain = (flags & LHAF_PLAIN_ACCUM) ? 1 : 0;
-  p.skip_mask = 0u;
-  p.wscale = 1.0;
-  p.bq = -1;
-  p.bA = 0;
-  p.n_items = pl.Hl * (pl.Hl - 1) / 2;
-  p.team_bytes = (int)team_shared_bytes(fp32, pl.nd, pl.H, pl.P);
-  p.items_bytes =
-      (int)(cta_shared_bytes(fp32, team, pl.nd, pl.H, pl.Hl, pl.P) - (size_t)teams_per_cta(team) * p.team_bytes);
-  for (int q = 0; q < pl.P; q++) {
-    p.eta[q] = pl.eta[q];
-    p.radix[q] = pl.radix[q];
-  }
+  fill_params(pl, fp32, false, team, flags, p);  // the whole sieve on the full working matrix
   // Grid: at most one resident wave, and never more teams than the scratch holds partials for.
   const int tpc = teams_per_cta(team);
   uint64_t grid = (pl.T + tpc - 1) / tpc;

@@ -1,7 +1,7 @@
 """Bounded launches and checkpoint/resume on the 60-photon collision-free loop hafnian (working
-dimension 61, degree 30: the series is finished inside the team). Every launch of the sieve-term
-kernel covers at most the flop budget, its per-term partials are reduced in term order (the same
-bits for the same range whichever CTA took which term), and a sum interrupted between chunks and
+dimension 61, degree 30), with the series staged (the default up to degree 32) and finished inside
+the team. Every launch of the sieve-term kernel covers at most the flop budget, its terms are
+summed in term order (the same bits for the same range whichever CTA took which term), and a sum interrupted between chunks and
 resumed from its checkpoint equals the uninterrupted one bit for bit (App. B.6: the terms are
 independent, so range partials add)."""
 import math
@@ -39,7 +39,10 @@ def _val(part):
     return complex(part[0] + part[1], part[2] + part[3])
 
 
-def test_launch_budget_splits_and_agrees(ctx, lg, p60, monkeypatch):
+@pytest.mark.parametrize("series", ["staged", "inline"])
+def test_launch_budget_splits_and_agrees(ctx, lg, p60, monkeypatch, series):
+    if series == "inline":  # the series finished inside the team, per-term partials in term order
+        monkeypatch.setenv("LHAF_STAGE", "0")
     S = 1 << 13
     T, nd, h, _ = lg.plan(p60.reps)
     assert (T, nd, h) == (1 << 29, 61, 30)

@@ -183,10 +183,13 @@ def test_working_dimension_classes_same_value(ctx, lg, monkeypatch, force):
     assert rel(ctx.lhaf(p.B, p.gamma, p.reps), ref) < TOL
     q = wl.small_problem(seed=5, M=7, reps=(2, 1, 1, 3, 1, 2, 1), loops=True)
     assert rel(ctx.lhaf(q.B, q.gamma, q.reps, flags=lg.ET), lo.lhaf_repeated(q.B, q.gamma, q.reps)) < TOL
-    # degree 25: the series run inline in the terms kernel (no staging), 16 zero-digit groups
-    # (a well-conditioned instance: sum |terms| / |sum| = 3.9e3)
+    # degree 25, 16 zero-digit groups (a well-conditioned instance: sum |terms| / |sum| = 3.9e3),
+    # with the series staged (default up to degree 32) and inline in the terms kernel
     u = wl.small_problem(seed=2, M=8, reps=(8, 8, 8, 8, 6, 6, 4, 2), loops=True, scale=1.0)
-    assert rel(ctx.lhaf(u.B, u.gamma, u.reps), lo.lhaf_repeated(u.B, u.gamma, u.reps)) < TOL
+    ref_u = lo.lhaf_repeated(u.B, u.gamma, u.reps)
+    assert rel(ctx.lhaf(u.B, u.gamma, u.reps), ref_u) < TOL
+    monkeypatch.setenv("LHAF_STAGE", "0")
+    assert rel(ctx.lhaf(u.B, u.gamma, u.reps), ref_u) < TOL
 
 
 def test_zero_digit_range_partials_cross_groups(ctx, lg):
@@ -202,13 +205,16 @@ def test_zero_digit_range_partials_cross_groups(ctx, lg):
         ctx.lhaf_range(p.B, p.gamma, p.reps, 0, T + 1)
 
 
+@pytest.mark.parametrize("series", ["staged", "inline"])
 @pytest.mark.parametrize("loops", [False, True])
-def test_zero_digit_groups_inline_series(ctx, lg, loops):
+def test_zero_digit_groups_inline_series(ctx, lg, loops, series, monkeypatch):
     # h = 25 > the staged-series limit: the groups finish their series inside the team. Repeat
     # counts 6-7 make the signed sum cancel by ~1e8 (sum |terms| / |lhaf|), beyond what an FP64
     # sum can resolve to 1e-10, so the reference is the oracle in extended precision and the bar
     # is the forward error of the sum: 1e-13 * sum |terms| * 2^-h (each term carries a relative
     # error of order 1e-15; measured about 1e-15).
+    if series == "inline":
+        monkeypatch.setenv("LHAF_STAGE", "0")
     reps = (7, 7, 6, 6, 6, 6, 6, 6)
     p = wl.small_problem(seed=77, M=len(reps), reps=reps, loops=loops)
     ref = complex(lo.lhaf_repeated(p.B, p.gamma, p.reps, dtype=np.clongdouble))
@@ -219,13 +225,14 @@ def test_zero_digit_groups_inline_series(ctx, lg, loops):
     assert abs(got - ref) <= 1e-13 * scale and abs(full - ref) <= 1e-13 * scale
 
 
-def test_inline_series_well_conditioned(ctx, lg):
-    # h = 25 with single repeats over two modes: 13 terms, no zero-digit split
-    reps = (25, 25)
+@pytest.mark.parametrize("reps", [(25, 25), (33, 33)])
+def test_inline_series_well_conditioned(ctx, lg, reps):
+    # h = 25 (staged) and h = 33 (above the staging limit: inline) with single repeats over two
+    # modes, no zero-digit split
     p = wl.small_problem(seed=5, M=2, reps=reps, loops=True)
     ref = lo.lhaf_repeated(p.B, p.gamma, p.reps)
     got, st = ctx.lhaf(p.B, p.gamma, p.reps, stats=True)
-    assert st["h"] == 25 and lg.plan_groups(reps) == 0
+    assert st["h"] == reps[0] and lg.plan_groups(reps) == 0
     assert rel(got, ref) < TOL
 
 
