@@ -244,6 +244,21 @@ lhaf_status lhaf_multi_gamma(lhaf_ctx* ctx, int M, const lhaf_c128* B, int n_gam
 lhaf_status lhaf_grad(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128* gamma, const int32_t* reps,
                       uint32_t flags, lhaf_c128* value, lhaf_c128* dB, lhaf_c128* dgamma);
 
+/* lhaf_grad for a batch of outcomes of one state (the log-probability batches of a GBS training
+ * step): item i uses reps[i * M ..] and gammas[i * M ..] (gammas NULL: loops from diag(B)) with the
+ * shared M x M matrix B. All items' slot matrices go up in one copy, their adjoint launches and
+ * reductions run back to back on the context's stream, and one synchronisation ends the call.
+ *   values      : HOST, batch values.
+ *   dB          : HOST batch x M x M or NULL (as lhaf_grad, item after item).
+ *   dgamma      : HOST batch x M or NULL (written only when gammas is given).
+ *   item_status : HOST batch statuses or NULL. With it the call returns LHAF_OK once the batch ran
+ *                 and a failed item (bad counts or values, too large) has its status there and
+ *                 zeros in its outputs; without it the first item error is returned.
+ * Host pointers only (LHAF_DEVICE_PTRS and LHAF_FP32_TERMS give LHAF_EINVAL). */
+lhaf_status lhaf_grad_batched(lhaf_ctx* ctx, int batch, int M, const lhaf_c128* B, const lhaf_c128* gammas,
+                              const int32_t* reps, uint32_t flags, lhaf_c128* values, lhaf_c128* dB,
+                              lhaf_c128* dgamma, lhaf_status* item_status);
+
 /* GBS pattern probability of a pure Gaussian state (App. A, Eq. mixed_prob with the pure-state
  * block form Eq. Adef): squeezed vacuum in every mode (a -> a cosh r - a^dag sinh r), then the
  * interferometer a -> U a, then the displacement alpha. On the host: the complex covariance

@@ -96,6 +96,8 @@ def _lib():
         L.lhaf_multi_gamma.restype = c.c_int
         L.lhaf_grad.argtypes = [vp, c.c_int, vp, vp, vp, c.c_uint32, vp, vp, vp]
         L.lhaf_grad.restype = c.c_int
+        L.lhaf_grad_batched.argtypes = [vp, c.c_int, c.c_int, vp, vp, vp, c.c_uint32, vp, vp, vp, vp]
+        L.lhaf_grad_batched.restype = c.c_int
         L.lhaf_batched_plan_create.argtypes = [vp, c.c_int, c.c_int, vp, vp, vp, c.c_uint32, ctypes.POINTER(vp)]
         L.lhaf_batched_plan_create.restype = c.c_int
         L.lhaf_batched_plan_exec.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
@@ -408,6 +410,25 @@ class Context:
         _check(self._lib.lhaf_grad(self._h, M, Bh.ctypes.data, None if gh is None else gh.ctypes.data, _ptr(r), flags,
                                    val.ctypes.data, dB.ctypes.data, dg.ctypes.data), "lhaf_grad")
         return complex(val[0]), dB, (None if gh is None else dg)
+
+    def lhaf_grad_batched(self, B, gammas, reps, flags: int = 0):
+        """Values (batch,), dB (batch x M x M), dgamma (batch x M, or None when gammas is None) and
+        item statuses of the loop hafnians of `reps` (batch x M) with the shared matrix B."""
+        Bh = _host_c128(B)
+        M = Bh.shape[0]
+        r = np.ascontiguousarray(np.asarray(reps, dtype=np.int32))
+        if r.ndim != 2 or r.shape[1] != M:
+            raise ValueError("reps must be batch x M")
+        batch = r.shape[0]
+        gh = None if gammas is None else np.ascontiguousarray(np.asarray(gammas, dtype=np.complex128).reshape(batch, M))
+        vals = np.zeros(batch, np.complex128)
+        dB = np.zeros((batch, M, M), np.complex128)
+        dg = np.zeros((batch, M), np.complex128)
+        st = np.zeros(batch, np.int32)
+        _check(self._lib.lhaf_grad_batched(self._h, batch, M, Bh.ctypes.data, None if gh is None else gh.ctypes.data,
+                                           r.ctypes.data, flags, vals.ctypes.data, dB.ctypes.data, dg.ctypes.data,
+                                           st.ctypes.data), "lhaf_grad_batched")
+        return vals, dB, (None if gh is None else dg), st
 
 
 class BatchedPlan:

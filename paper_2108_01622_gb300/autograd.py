@@ -38,6 +38,34 @@ class LoopHafnian(torch.autograd.Function):
         return gB, gg, None, None
 
 
+class LoopHafnianBatch(torch.autograd.Function):
+    """lhaf(B_{n_i}) for a batch of patterns with one shared B and per-item loop weights, the
+    gradients from one lhaf_grad_batched call."""
+
+    @staticmethod
+    def forward(fctx, B, gammas, reps, lib_ctx):
+        Bn = B.detach().cpu().numpy()
+        gn = gammas.detach().cpu().numpy()
+        vals, dB, dg, st = lib_ctx.lhaf_grad_batched(Bn, gn, reps)
+        if np.any(st != 0):
+            raise RuntimeError(f"lhaf_grad_batched item statuses {st[st != 0][:8]}")
+        fctx.save_for_backward(torch.from_numpy(np.triu(dB)).to(B.device), torch.from_numpy(dg).to(B.device))
+        return torch.from_numpy(vals).to(B.device)
+
+    @staticmethod
+    def backward(fctx, grad_out):
+        dB, dg = fctx.saved_tensors
+        gB = torch.einsum("b,bij->ij", grad_out, dB.conj())
+        gg = grad_out[:, None] * dg.conj()
+        return gB, gg, None, None
+
+
+def lhaf_batch_torch(B: torch.Tensor, gammas: torch.Tensor, reps, lib_ctx: Context) -> torch.Tensor:
+    """lhaf(B_{n_i}) for reps (batch x M) as a differentiable complex128 vector (B shared, gammas
+    batch x M)."""
+    return LoopHafnianBatch.apply(B, gammas, np.asarray(reps, dtype=np.int32), lib_ctx)
+
+
 def lhaf_torch(B: torch.Tensor, gamma, reps, lib_ctx: Context) -> torch.Tensor:
     """lhaf(B_n) as a differentiable complex128 scalar (B, gamma: complex128 tensors)."""
     return LoopHafnian.apply(B, gamma, np.asarray(reps, dtype=np.int32), lib_ctx)
@@ -71,3 +99,14 @@ def gbs_log_prob_torch(U, r, alpha, n, lib_ctx: Context) -> torch.Tensor:
     B, g, logP0 = pure_state_kernel_torch(U, r, alpha)
     lh = lhaf_torch(B, g, n, lib_ctx)
     return logP0 + torch.log((lh * lh.conj()).real) - sum(math.lgamma(int(k) + 1) for k in n)
+
+
+def gbs_log_prob_batch_torch(U, r, alpha, ns, lib_ctx: Context) -> torch.Tensor:
+    """log P(n_i) for a batch of outcomes ns (batch x M) of one pure state, differentiable in U, r
+    and alpha; the loop hafnians and their gradients come from one lhaf_grad_batched call."""
+    B, g, logP0 = pure_state_kernel_torch(U, r, alpha)
+    ns = np.asarray(ns, dtype=np.int32)
+    lh = lhaf_batch_torch(B, g.unsqueeze(0).expand(ns.shape[0], -1).contiguous(), ns, lib_ctx)
+    fact = torch.tensor([sum(math.lgamma(int(k) + 1) for k in row) for row in ns], dtype=torch.float64,
+                        device=lh.device)
+    return logP0 + torch.log((lh * lh.conj()).real) - fact
