@@ -426,175 +426,220 @@ def run_extras(ctx, torch, dev, lg, workload):
     from paper_2108_01622_gb300 import workloads as wl
 
     out = {}
-    if workload == "large60":
-        # the 40-photon collision pattern (100 modes, counts 1..4, gamma = 0): whole calls
-        p = wl.collision_lhaf_40(seed=2)
-        T, nd, h, _ = lg.plan(p.reps, has_loops=False)
-        Bd = torch.from_numpy(p.B).to(dev)
-        gd = torch.from_numpy(p.gamma).to(dev)
-        o = torch.empty(1, dtype=torch.complex128, device=dev)
-        ctx.lhaf(Bd, gd, p.reps, flags=lg.NO_LOOPS, out=o)
-        ks, fl = [], 0.0
-        for _ in range(10):
-            _, st = ctx.lhaf(Bd, gd, p.reps, flags=lg.NO_LOOPS, out=o, stats=True)
-            ks.append(st["kernel_ms"])
-            fl = st["flops_model"]
-        ms = _timed(torch, lambda: ctx.lhaf(Bd, gd, p.reps, flags=lg.NO_LOOPS, out=o), reps=10)
-        out["collision40"] = {"workload": WORKLOADS["collision40"]["desc"], "terms": T, "n_dim": nd, "h": h,
-                              "ms_per_lhaf": ms, "terms_per_s": T / (ms * 1e-3),
-                              "kernel_tflops": fl / (statistics.median(ks) * 1e-3) / 1e12,
-                              "kernel_frac": fl / (statistics.median(ks) * 1e-3) / 1e12 / NOMINAL_FP64_TFLOPS}
-        # plain FP64 accumulation against double-double on a 2^17-term slice of the 60-photon sum
-        p60 = wl.large_lhaf_60(seed=5)
-        S = 1 << 17
-        pd = ctx.lhaf_range(p60.B, p60.gamma, p60.reps, 0, S)
-        pp = ctx.lhaf_range(p60.B, p60.gamma, p60.reps, 0, S, flags=lg.PLAIN_ACCUM)
-        sd, sp = complex(pd[0] + pd[1], pd[2] + pd[3]), complex(pp[0] + pp[1], pp[2] + pp[3])
-        out["lhaf60_plain_accum"] = {"slice_terms": S, "plain_vs_dd_rel_diff": abs(sp - sd) / abs(sd)}
-    # batched vs one call per item: the 4096 loop hafnians of the chain-rule batch (N in 10..40)
-    b = wl.chain_rule_batch(seed=3, count=4096)
-    R = np.array(b.reps)
-    Gd = torch.from_numpy(np.array(b.gammas)).to(dev)
-    Bd = torch.from_numpy(b.B).to(dev)
-    ob = torch.empty(len(R), dtype=torch.complex128, device=dev)
-    op = torch.empty(len(R), dtype=torch.complex128, device=dev)
-    og = torch.empty(len(R), dtype=torch.complex128, device=dev)
-    ctx.lhaf_batched(Bd, Gd, R, out=ob)
 
-    def plain():
-        for i in range(len(R)):
-            ctx.lhaf(Bd, Gd[i], R[i], out=op[i:i + 1])
+    def _collision40_and_plain_accum():
+        if workload == "large60":
+            # the 40-photon collision pattern (100 modes, counts 1..4, gamma = 0): whole calls
+            p = wl.collision_lhaf_40(seed=2)
+            T, nd, h, _ = lg.plan(p.reps, has_loops=False)
+            Bd = torch.from_numpy(p.B).to(dev)
+            gd = torch.from_numpy(p.gamma).to(dev)
+            o = torch.empty(1, dtype=torch.complex128, device=dev)
+            ctx.lhaf(Bd, gd, p.reps, flags=lg.NO_LOOPS, out=o)
+            ks, fl = [], 0.0
+            for _ in range(10):
+                _, st = ctx.lhaf(Bd, gd, p.reps, flags=lg.NO_LOOPS, out=o, stats=True)
+                ks.append(st["kernel_ms"])
+                fl = st["flops_model"]
+            ms = _timed(torch, lambda: ctx.lhaf(Bd, gd, p.reps, flags=lg.NO_LOOPS, out=o), reps=10)
+            out["collision40"] = {"workload": WORKLOADS["collision40"]["desc"], "terms": T, "n_dim": nd, "h": h,
+                                  "ms_per_lhaf": ms, "terms_per_s": T / (ms * 1e-3),
+                                  "kernel_tflops": fl / (statistics.median(ks) * 1e-3) / 1e12,
+                                  "kernel_frac": fl / (statistics.median(ks) * 1e-3) / 1e12 / NOMINAL_FP64_TFLOPS}
+            # plain FP64 accumulation against double-double on a 2^17-term slice of the 60-photon sum
+            p60 = wl.large_lhaf_60(seed=5)
+            S = 1 << 17
+            pd = ctx.lhaf_range(p60.B, p60.gamma, p60.reps, 0, S)
+            pp = ctx.lhaf_range(p60.B, p60.gamma, p60.reps, 0, S, flags=lg.PLAIN_ACCUM)
+            sd, sp = complex(pd[0] + pd[1], pd[2] + pd[3]), complex(pp[0] + pp[1], pp[2] + pp[3])
+            out["lhaf60_plain_accum"] = {"slice_terms": S, "plain_vs_dd_rel_diff": abs(sp - sd) / abs(sd)}
 
-    plain()  # warms the per-shape tuning cache of the single-call path
-    torch.cuda.synchronize()
-    tb = _timed(torch, lambda: ctx.lhaf_batched(Bd, Gd, R, out=ob), reps=1)
-    tp = _timed(torch, plain, reps=1)
-    with ctx.batched_plan(Bd, Gd, R) as plan:
-        plan.run(Bd, Gd, out=og)
-        tg_ = _timed(torch, lambda: plan.run(Bd, Gd, out=og), reps=1)
-    d = torch.maximum((ob - op).abs() / op.abs(), (og - op).abs() / op.abs())
-    out["batched"] = {"workload": "chain-rule batch: 4096 loop hafnians, 50-mode lossy GBS state, N~U{10..40}",
-                      "batched_ms": tb, "graph_replay_ms": tg_, "plain_ms": tp,
-                      "batched_over_plain_speedup": tp / tb, "graph_over_plain_speedup": tp / tg_,
-                      "max_rel_diff": float(d.max().item())}
-    # small items only: many short loop hafnians, where one launch per item is launch-bound
-    bs = wl.chain_rule_batch(seed=7, count=2048, n_lo=8, n_hi=16)
-    Rs = np.array(bs.reps)
-    Gs = torch.from_numpy(np.array(bs.gammas)).to(dev)
-    Bs = torch.from_numpy(bs.B).to(dev)
-    obs = torch.empty(len(Rs), dtype=torch.complex128, device=dev)
-    ops_ = torch.empty(len(Rs), dtype=torch.complex128, device=dev)
-    ctx.lhaf_batched(Bs, Gs, Rs, out=obs)
+    def _batched():
+        # batched vs one call per item: the 4096 loop hafnians of the chain-rule batch (N in 10..40)
+        b = wl.chain_rule_batch(seed=3, count=4096)
+        R = np.array(b.reps)
+        Gd = torch.from_numpy(np.array(b.gammas)).to(dev)
+        Bd = torch.from_numpy(b.B).to(dev)
+        ob = torch.empty(len(R), dtype=torch.complex128, device=dev)
+        op = torch.empty(len(R), dtype=torch.complex128, device=dev)
+        og = torch.empty(len(R), dtype=torch.complex128, device=dev)
+        ctx.lhaf_batched(Bd, Gd, R, out=ob)
 
-    def plain_s():
-        for i in range(len(Rs)):
-            ctx.lhaf(Bs, Gs[i], Rs[i], out=ops_[i:i + 1])
+        def plain():
+            for i in range(len(R)):
+                ctx.lhaf(Bd, Gd[i], R[i], out=op[i:i + 1])
 
-    plain_s()
-    tbs = _timed(torch, lambda: ctx.lhaf_batched(Bs, Gs, Rs, out=obs), reps=2)
-    tps = _timed(torch, plain_s, reps=2)
-    ogs = torch.empty(len(Rs), dtype=torch.complex128, device=dev)
-    with ctx.batched_plan(Bs, Gs, Rs) as plan:
-        plan.run(Bs, Gs, out=ogs)
-        tgs = _timed(torch, lambda: plan.run(Bs, Gs, out=ogs), reps=3)
-    out["batched_small"] = {"workload": "2048 loop hafnians, N~U{8..16}, same state family",
-                            "batched_ms": tbs, "graph_replay_ms": tgs, "plain_ms": tps,
-                            "batched_over_plain_speedup": tps / tbs, "graph_over_plain_speedup": tps / tgs}
-    # batched mode of one chain-rule step (App. B.5): the next mode's outcomes n = 0..8 at once,
-    # against the same nine loop hafnians as one batch
-    cb = wl.chain_rule_batch(seed=11, count=64, n_lo=26, n_hi=30)
-    ci = max(range(len(cb.reps)), key=lambda i: int(np.sum(cb.reps[i])))
-    fixed = np.array(cb.reps[ci], dtype=np.int32)
-    mode = int(np.nonzero(fixed == 0)[0][0])
-    gm = np.array(cb.gammas[ci])
-    n_cut = 8
-    pats = np.repeat(fixed[None, :], n_cut + 1, axis=0)
-    pats[:, mode] = np.arange(n_cut + 1)
-    gms = np.repeat(gm[None, :], n_cut + 1, axis=0)
-    ctx.lhaf_batched_mode(cb.B, gm, fixed, mode, n_cut)
-    ctx.lhaf_batched(cb.B, gms, pats)
-    tm = _timed(torch, lambda: ctx.lhaf_batched_mode(cb.B, gm, fixed, mode, n_cut), reps=3)
-    tbp = _timed(torch, lambda: ctx.lhaf_batched(cb.B, gms, pats), reps=3)
-    ctx.lhaf(cb.B, gm, pats[-1])
-    tl = _timed(torch, lambda: ctx.lhaf(cb.B, gm, pats[-1]), reps=3)
-    vm = ctx.lhaf_batched_mode(cb.B, gm, fixed, mode, n_cut)
-    vb, _ = ctx.lhaf_batched(cb.B, gms, pats)
-    out["batched_mode"] = {"workload": f"chain-rule step: {int(fixed.sum())} fixed photons, outcomes 0..{n_cut} "
-                                       "of the next mode, 50-mode lossy state",
-                           "batched_mode_ms": tm, "batched_patterns_ms": tbp, "speedup": tbp / tm,
-                           "largest_outcome_alone_ms": tl, "batched_mode_over_largest": tm / tl,
-                           "max_rel_diff": float(np.max(np.abs(vm - vb) / np.abs(vb)))}
-    # several loop-weight vectors on one pattern (App. B.5, threshold sub-detectors): 16 vectors on
-    # the 40-photon collision pattern, against the same 16 loop hafnians as one batch
-    pm_ = wl.collision_lhaf_40(seed=2)
-    Gm = wl.complex_normal(np.random.default_rng(21), (16, len(pm_.reps)))
-    Rm = np.repeat(np.asarray(pm_.reps)[None, :], 16, axis=0)
-    vm_ = ctx.lhaf_multi_gamma(pm_.B, Gm, pm_.reps)
-    vb_, _ = ctx.lhaf_batched(pm_.B, Gm, Rm)
-    tmg = _timed(torch, lambda: ctx.lhaf_multi_gamma(pm_.B, Gm, pm_.reps), reps=3)
-    tbg = _timed(torch, lambda: ctx.lhaf_batched(pm_.B, Gm, Rm), reps=3)
-    out["multi_gamma"] = {"workload": "16 loop-weight vectors on the 40-photon collision pattern (100-mode Haar)",
-                          "multi_gamma_ms": tmg, "batched_ms": tbg, "speedup": tbg / tmg,
-                          "max_rel_diff": float(np.max(np.abs(vm_ - vb_) / np.abs(vb_)))}
-    # one chain-rule step (App. A.2): a 50-mode pure state, 20 photons sampled on half of the
-    # modes, coherent amplitudes on the rest, the next mode's distribution over 0..8
-    rng_c = np.random.default_rng(31)
-    Uc = wl.haar_unitary(rng_c, 50)
-    rc = rng_c.uniform(0.8, 1.2, size=50)
-    ac = wl.complex_normal(rng_c, 50, 0.1)
-    nc = np.zeros(50, dtype=np.int32)
-    nc[:25] = wl.pattern_multinomial(rng_c, 25, 20, 3)
-    bc = wl.complex_normal(rng_c, 50, 1.0)
-    bc[:26] = 0.0
-    ctx.gbs_chain_rule_step(Uc, rc, ac, bc, nc, 25, 8, u=0.5)
-    tcs = _timed(torch, lambda: ctx.gbs_chain_rule_step(Uc, rc, ac, bc, nc, 25, 8, u=0.5), reps=3)
-    out["chain_rule_step"] = {"workload": "50-mode pure state, 20 photons on modes 0..24, coherent amplitudes on "
-                                          "26..49, distribution of mode 25 over 0..8 and one draw",
-                              "ms": tcs}
-    # mixed state (App. B.2 lhafmix): a 20-photon outcome of a 50-mode lossy state, the loop
-    # hafnian of the 100 x 100 matrix A with every occupied index pair repeated
-    ms_ = wl.lossy_state(seed=12, M=50, r_lo=0.8, r_hi=1.4, eta=0.6)
-    nm = wl.pattern_multinomial(np.random.default_rng(12), 50, 20, 3)
-    Tm, ndm, hm, _ = lg.plan(np.concatenate([nm, nm]))
-    ctx.gbs_pattern_prob_mixed(ms_.sigma, ms_.alpha, nm)
-    tmx = _timed(torch, lambda: ctx.gbs_pattern_prob_mixed(ms_.sigma, ms_.alpha, nm), reps=3)
-    out["mixed"] = {"workload": "P(n) of a 20-photon outcome (counts <= 3) of a 50-mode lossy state, eta = 0.6",
-                    "terms": Tm, "n_dim": ndm, "h": hm, "ms": tmx}
-    # eigenvalue-trace variant against the finite difference sieve (App. B.4, Fig. glynn_accuracy):
-    # relative error of lhaf(A1 (+) A2) against lhaf(A1) lhaf(A2) (halves by the sieve, each pair
-    # crossing the blocks), and the time of one N = 40 loop hafnian by each
-    acc = {}
-    for n_half in (12, 16, 20):
-        ef, ee, epl = [], [], []
-        for sd in range(5):
-            bp = wl.block_diagonal_pair(seed=1000 * n_half + sd, n=n_half)
-            ones_h = [1] * n_half
-            ref = ctx.lhaf(bp.A1, None, ones_h) * ctx.lhaf(bp.A2, None, ones_h)
-            ones = [1] * (2 * n_half)
-            ef.append(abs(ctx.lhaf(bp.C, None, ones) - ref) / abs(ref))
-            ee.append(abs(ctx.lhaf(bp.C, None, ones, flags=lg.ET) - ref) / abs(ref))
-            epl.append(abs(ctx.lhaf(bp.C, None, ones, flags=lg.PLAIN_ACCUM) - ref) / abs(ref))
-        acc[str(2 * n_half)] = {"fds_median": float(np.median(ef)), "fds_max": float(max(ef)),
-                                "fds_plain_accum_median": float(np.median(epl)),
-                                "fds_plain_accum_max": float(max(epl)),
-                                "et_median": float(np.median(ee)), "et_max": float(max(ee))}
-    bp = wl.block_diagonal_pair(seed=7, n=20)
-    ones = [1] * 40
-    tf = _timed(torch, lambda: ctx.lhaf(bp.C, None, ones), reps=3)
-    te_ = _timed(torch, lambda: ctx.lhaf(bp.C, None, ones, flags=lg.ET), reps=3)
-    out["et_vs_fds"] = {"workload": "block-diagonal A1 (+) A2 of random complex symmetric halves, loops on the "
-                                    "diagonal, one photon per index, 5 instances per N",
-                        "relative_error_by_N": acc, "fds_ms_N40": tf, "et_ms_N40": te_,
-                        "fds_terms_N40": lg.plan(ones)[0], "et_terms_N40": lg.plan(ones, flags=lg.ET)[0]}
-    # adjoint: one 32-photon outcome of a 40-mode state (CUDA events around the host-pointer calls)
-    gb = wl.gradient_batch(seed=4, count=2)
-    ctx.lhaf_grad(gb.B, gb.gammas[0], gb.reps[0])
-    ctx.lhaf(gb.B, gb.gammas[0], gb.reps[0])
-    tg = _timed(torch, lambda: ctx.lhaf_grad(gb.B, gb.gammas[0], gb.reps[0]), reps=3)
-    tv = _timed(torch, lambda: ctx.lhaf(gb.B, gb.gammas[0], gb.reps[0]), reps=3)
-    Tg, ndg, hg, _ = lg.plan(gb.reps[0])
-    out["grad"] = {"workload": "value + d/dB + d/dgamma of one 32-photon outcome, 40-mode state",
-                   "terms": Tg, "n_dim": ndg, "h": hg, "grad_ms": tg, "value_ms": tv, "grad_over_value": tg / tv}
+        plain()  # warms the per-shape tuning cache of the single-call path
+        torch.cuda.synchronize()
+        tb = _timed(torch, lambda: ctx.lhaf_batched(Bd, Gd, R, out=ob), reps=1)
+        tp = _timed(torch, plain, reps=1)
+        with ctx.batched_plan(Bd, Gd, R) as plan:
+            plan.run(Bd, Gd, out=og)
+            tg_ = _timed(torch, lambda: plan.run(Bd, Gd, out=og), reps=1)
+        d = torch.maximum((ob - op).abs() / op.abs(), (og - op).abs() / op.abs())
+        out["batched"] = {"workload": "chain-rule batch: 4096 loop hafnians, 50-mode lossy GBS state, N~U{10..40}",
+                          "batched_ms": tb, "graph_replay_ms": tg_, "plain_ms": tp,
+                          "batched_over_plain_speedup": tp / tb, "graph_over_plain_speedup": tp / tg_,
+                          "max_rel_diff": float(d.max().item())}
+
+    def _batched_small():
+        # small items only: many short loop hafnians, where one launch per item is launch-bound
+        bs = wl.chain_rule_batch(seed=7, count=2048, n_lo=8, n_hi=16)
+        Rs = np.array(bs.reps)
+        Gs = torch.from_numpy(np.array(bs.gammas)).to(dev)
+        Bs = torch.from_numpy(bs.B).to(dev)
+        obs = torch.empty(len(Rs), dtype=torch.complex128, device=dev)
+        ops_ = torch.empty(len(Rs), dtype=torch.complex128, device=dev)
+        ctx.lhaf_batched(Bs, Gs, Rs, out=obs)
+
+        def plain_s():
+            for i in range(len(Rs)):
+                ctx.lhaf(Bs, Gs[i], Rs[i], out=ops_[i:i + 1])
+
+        plain_s()
+        tbs = _timed(torch, lambda: ctx.lhaf_batched(Bs, Gs, Rs, out=obs), reps=2)
+        tps = _timed(torch, plain_s, reps=2)
+        ogs = torch.empty(len(Rs), dtype=torch.complex128, device=dev)
+        with ctx.batched_plan(Bs, Gs, Rs) as plan:
+            plan.run(Bs, Gs, out=ogs)
+            tgs = _timed(torch, lambda: plan.run(Bs, Gs, out=ogs), reps=3)
+        out["batched_small"] = {"workload": "2048 loop hafnians, N~U{8..16}, same state family",
+                                "batched_ms": tbs, "graph_replay_ms": tgs, "plain_ms": tps,
+                                "batched_over_plain_speedup": tps / tbs, "graph_over_plain_speedup": tps / tgs}
+
+    def _batched_mode():
+        # batched mode of one chain-rule step (App. B.5): the next mode's outcomes n = 0..8 at once,
+        # against the same nine loop hafnians as one batch
+        cb = wl.chain_rule_batch(seed=11, count=64, n_lo=26, n_hi=30)
+        ci = max(range(len(cb.reps)), key=lambda i: int(np.sum(cb.reps[i])))
+        fixed = np.array(cb.reps[ci], dtype=np.int32)
+        mode = int(np.nonzero(fixed == 0)[0][0])
+        gm = np.array(cb.gammas[ci])
+        n_cut = 8
+        pats = np.repeat(fixed[None, :], n_cut + 1, axis=0)
+        pats[:, mode] = np.arange(n_cut + 1)
+        gms = np.repeat(gm[None, :], n_cut + 1, axis=0)
+        ctx.lhaf_batched_mode(cb.B, gm, fixed, mode, n_cut)
+        ctx.lhaf_batched(cb.B, gms, pats)
+        tm = _timed(torch, lambda: ctx.lhaf_batched_mode(cb.B, gm, fixed, mode, n_cut), reps=3)
+        tbp = _timed(torch, lambda: ctx.lhaf_batched(cb.B, gms, pats), reps=3)
+        ctx.lhaf(cb.B, gm, pats[-1])
+        tl = _timed(torch, lambda: ctx.lhaf(cb.B, gm, pats[-1]), reps=3)
+        vm = ctx.lhaf_batched_mode(cb.B, gm, fixed, mode, n_cut)
+        vb, _ = ctx.lhaf_batched(cb.B, gms, pats)
+        out["batched_mode"] = {"workload": f"chain-rule step: {int(fixed.sum())} fixed photons, outcomes 0..{n_cut} "
+                                           "of the next mode, 50-mode lossy state",
+                               "batched_mode_ms": tm, "batched_patterns_ms": tbp, "speedup": tbp / tm,
+                               "largest_outcome_alone_ms": tl, "batched_mode_over_largest": tm / tl,
+                               "max_rel_diff": float(np.max(np.abs(vm - vb) / np.abs(vb)))}
+
+    def _multi_gamma():
+        # several loop-weight vectors on one pattern (App. B.5, threshold sub-detectors): 16 vectors on
+        # the 40-photon collision pattern, against the same 16 loop hafnians as one batch
+        pm_ = wl.collision_lhaf_40(seed=2)
+        Gm = wl.complex_normal(np.random.default_rng(21), (16, len(pm_.reps)))
+        Rm = np.repeat(np.asarray(pm_.reps)[None, :], 16, axis=0)
+        vm_ = ctx.lhaf_multi_gamma(pm_.B, Gm, pm_.reps)
+        vb_, _ = ctx.lhaf_batched(pm_.B, Gm, Rm)
+        tmg = _timed(torch, lambda: ctx.lhaf_multi_gamma(pm_.B, Gm, pm_.reps), reps=3)
+        tbg = _timed(torch, lambda: ctx.lhaf_batched(pm_.B, Gm, Rm), reps=3)
+        out["multi_gamma"] = {"workload": "16 loop-weight vectors on the 40-photon collision pattern (100-mode Haar)",
+                              "multi_gamma_ms": tmg, "batched_ms": tbg, "speedup": tbg / tmg,
+                              "max_rel_diff": float(np.max(np.abs(vm_ - vb_) / np.abs(vb_)))}
+
+    def _chain_rule_step():
+        # one chain-rule step (App. A.2): a 50-mode pure state, 20 photons sampled on half of the
+        # modes, coherent amplitudes on the rest, the next mode's distribution over 0..8
+        rng_c = np.random.default_rng(31)
+        Uc = wl.haar_unitary(rng_c, 50)
+        rc = rng_c.uniform(0.8, 1.2, size=50)
+        ac = wl.complex_normal(rng_c, 50, 0.1)
+        nc = np.zeros(50, dtype=np.int32)
+        nc[:25] = wl.pattern_multinomial(rng_c, 25, 20, 3)
+        bc = wl.complex_normal(rng_c, 50, 1.0)
+        bc[:26] = 0.0
+        ctx.gbs_chain_rule_step(Uc, rc, ac, bc, nc, 25, 8, u=0.5)
+        tcs = _timed(torch, lambda: ctx.gbs_chain_rule_step(Uc, rc, ac, bc, nc, 25, 8, u=0.5), reps=3)
+        out["chain_rule_step"] = {"workload": "50-mode pure state, 20 photons on modes 0..24, coherent amplitudes on "
+                                              "26..49, distribution of mode 25 over 0..8 and one draw",
+                                  "ms": tcs}
+
+    def _mixed():
+        # mixed state (App. B.2 lhafmix): a 20-photon outcome of a 50-mode lossy state, the loop
+        # hafnian of the 100 x 100 matrix A with every occupied index pair repeated
+        ms_ = wl.lossy_state(seed=12, M=50, r_lo=0.8, r_hi=1.4, eta=0.6)
+        nm = wl.pattern_multinomial(np.random.default_rng(12), 50, 20, 3)
+        Tm, ndm, hm, _ = lg.plan(np.concatenate([nm, nm]))
+        ctx.gbs_pattern_prob_mixed(ms_.sigma, ms_.alpha, nm)
+        tmx = _timed(torch, lambda: ctx.gbs_pattern_prob_mixed(ms_.sigma, ms_.alpha, nm), reps=3)
+        out["mixed"] = {"workload": "P(n) of a 20-photon outcome (counts <= 3) of a 50-mode lossy state, eta = 0.6",
+                        "terms": Tm, "n_dim": ndm, "h": hm, "ms": tmx}
+
+    def _et_vs_fds():
+        # eigenvalue-trace variant against the finite difference sieve (App. B.4, Fig. glynn_accuracy):
+        # relative error of lhaf(A1 (+) A2) against lhaf(A1) lhaf(A2) (halves by the sieve, each pair
+        # crossing the blocks), and the time of one N = 40 loop hafnian by each
+        acc = {}
+        for n_half in (12, 16, 20):
+            ef, ee, epl = [], [], []
+            for sd in range(5):
+                bp = wl.block_diagonal_pair(seed=1000 * n_half + sd, n=n_half)
+                ones_h = [1] * n_half
+                ref = ctx.lhaf(bp.A1, None, ones_h) * ctx.lhaf(bp.A2, None, ones_h)
+                ones = [1] * (2 * n_half)
+                ef.append(abs(ctx.lhaf(bp.C, None, ones) - ref) / abs(ref))
+                ee.append(abs(ctx.lhaf(bp.C, None, ones, flags=lg.ET) - ref) / abs(ref))
+                epl.append(abs(ctx.lhaf(bp.C, None, ones, flags=lg.PLAIN_ACCUM) - ref) / abs(ref))
+            acc[str(2 * n_half)] = {"fds_median": float(np.median(ef)), "fds_max": float(max(ef)),
+                                    "fds_plain_accum_median": float(np.median(epl)),
+                                    "fds_plain_accum_max": float(max(epl)),
+                                    "et_median": float(np.median(ee)), "et_max": float(max(ee))}
+        bp = wl.block_diagonal_pair(seed=7, n=20)
+        ones = [1] * 40
+        tf = _timed(torch, lambda: ctx.lhaf(bp.C, None, ones), reps=3)
+        te_ = _timed(torch, lambda: ctx.lhaf(bp.C, None, ones, flags=lg.ET), reps=3)
+        out["et_vs_fds"] = {"workload": "block-diagonal A1 (+) A2 of random complex symmetric halves, loops on the "
+                                        "diagonal, one photon per index, 5 instances per N",
+                            "relative_error_by_N": acc, "fds_ms_N40": tf, "et_ms_N40": te_,
+                            "fds_terms_N40": lg.plan(ones)[0], "et_terms_N40": lg.plan(ones, flags=lg.ET)[0]}
+
+    def _grad():
+        # adjoint: one 32-photon outcome of a 40-mode state (CUDA events around the host-pointer calls)
+        gb = wl.gradient_batch(seed=4, count=2)
+        ctx.lhaf_grad(gb.B, gb.gammas[0], gb.reps[0])
+        ctx.lhaf(gb.B, gb.gammas[0], gb.reps[0])
+        tg = _timed(torch, lambda: ctx.lhaf_grad(gb.B, gb.gammas[0], gb.reps[0]), reps=3)
+        tv = _timed(torch, lambda: ctx.lhaf(gb.B, gb.gammas[0], gb.reps[0]), reps=3)
+        Tg, ndg, hg, _ = lg.plan(gb.reps[0])
+        out["grad"] = {"workload": "value + d/dB + d/dgamma of one 32-photon outcome, 40-mode state",
+                       "terms": Tg, "n_dim": ndg, "h": hg, "grad_ms": tg, "value_ms": tv, "grad_over_value": tg / tv}
+
+    def _grad_batch():
+        # the differentiated workload: 256 log-probability outcomes of 32 photons (40-mode state),
+        # values and gradients from one lhaf_grad_batched call, against the values alone batched
+        gb = wl.gradient_batch(seed=4, count=256)
+        R = np.stack(gb.reps).astype(np.int32)
+        G = np.stack(gb.gammas)
+        ctx.lhaf_grad_batched(gb.B, G[:2], R[:2])
+        ctx.lhaf_batched(gb.B, G, R)
+        tg = _timed(torch, lambda: ctx.lhaf_grad_batched(gb.B, G, R), reps=1)
+        tv = _timed(torch, lambda: ctx.lhaf_batched(gb.B, G, R), reps=2)
+        vals, _, _, st = ctx.lhaf_grad_batched(gb.B, G[:8], R[:8])
+        vb, _ = ctx.lhaf_batched(gb.B, G[:8], R[:8])
+        out["grad_batch"] = {"workload": "values and d/dB, d/dgamma of 256 outcomes of 32 photons, 40-mode state",
+                             "grad_batched_ms": tg, "values_batched_ms": tv, "grad_over_value": tg / tv,
+                             "value_max_rel_diff": float(np.max(np.abs(vals - vb) / np.abs(vb))),
+                             "items_ok": int(np.sum(st == 0))}
+
+    steps = (("collision40_and_plain_accum", _collision40_and_plain_accum), ("batched", _batched),
+             ("batched_small", _batched_small), ("batched_mode", _batched_mode), ("multi_gamma", _multi_gamma),
+             ("chain_rule_step", _chain_rule_step), ("mixed", _mixed), ("et_vs_fds", _et_vs_fds), ("grad", _grad),
+             ("grad_batch", _grad_batch))
+    for name, f in steps:
+        try:
+            f()
+        except Exception as e:  # one failing extra leaves the rest and the headline
+            out.setdefault("extras_errors", {})[name] = repr(e)[:400]
     return out
 
 
