@@ -355,7 +355,12 @@ def run_ours(args, rank, world, local_rank):
     n_slots = nd - (1 if loops else 0)
     survey_flops = survey_flops_per_term(n_slots, h) * (T_timed if whole_sum else T_all * args.steps)
     tr = KERNEL_TRAFFIC.get(args.workload)
-    traffic = tr[1] if (tr and tr[0] == kernel_source_sha()) else None
+    traffic = None
+    if tr and tr[0] == kernel_source_sha():
+        # the captured launch's DRAM bytes scaled to this run's average launch by its terms (the
+        # traffic is the staged term polynomials, proportional to the terms of a launch)
+        terms_per_launch = (T_timed if whole_sum else T_all * args.steps) / max(term_launches, 1)
+        traffic = tr[1] * terms_per_launch / tr[2]
     roofline = {"bound": "alu", "kernel": "grouped_terms_kernel (FP64 sieve terms)", "achieved": achieved,
                 "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s", "frac": achieved / NOMINAL_FP64_TFLOPS,
                 "traffic": traffic, "peak_source": PEAK_SOURCE + " (no FP64 entry is measured by the pool)",
@@ -368,8 +373,9 @@ def run_ours(args, rank, world, local_rank):
                 "survey_model_note": ("F(n,h) = (40/3+4/3) n^3 + 8 min(h-1,n) n^2 + 8 h^2 assumes a Householder "
                                       "reduction (twice the elimination's flops) and separate loop products; "
                                       "above 1 for this kernel, so the implementation model is the reported frac"),
-                "traffic_note": ("DRAM bytes of one full-size launch from an ncu capture of the current kernel "
-                                 "source" if traffic is not None else "no ncu capture of the current kernel source")}
+                "traffic_note": ("DRAM read + write bytes of one launch from an ncu capture of the current kernel "
+                                 "source, scaled to the average launch by its terms" if traffic is not None
+                                 else "no ncu capture of the current kernel source")}
     cfg = {"workload": meta["desc"], "evaluated_terms": T_all, "timed_terms": T_timed, "n_dim": nd, "h": h,
            "pairs": P, "team": st["team"], "zero_digit_groups": groups,
            "l2": "flushed between steps (256 MiB write, outside step events)",
@@ -523,14 +529,19 @@ def run_extras(ctx, torch, dev, lg, workload):
         ctx.lhaf_batched(cb.B, gms, pats)
         tm = _timed(torch, lambda: ctx.lhaf_batched_mode(cb.B, gm, fixed, mode, n_cut), reps=3)
         tbp = _timed(torch, lambda: ctx.lhaf_batched(cb.B, gms, pats), reps=3)
-        ctx.lhaf(cb.B, gm, pats[-1])
-        tl = _timed(torch, lambda: ctx.lhaf(cb.B, gm, pats[-1]), reps=3)
+        # the costliest single outcome (not necessarily the last: an odd count can add a pair)
+        t_each = []
+        for pat in pats:
+            ctx.lhaf(cb.B, gm, pat)
+            t_each.append(_timed(torch, lambda: ctx.lhaf(cb.B, gm, pat), reps=3))
+        tl = max(t_each)
         vm = ctx.lhaf_batched_mode(cb.B, gm, fixed, mode, n_cut)
         vb, _ = ctx.lhaf_batched(cb.B, gms, pats)
         out["batched_mode"] = {"workload": f"chain-rule step: {int(fixed.sum())} fixed photons, outcomes 0..{n_cut} "
                                            "of the next mode, 50-mode lossy state",
                                "batched_mode_ms": tm, "batched_patterns_ms": tbp, "speedup": tbp / tm,
                                "largest_outcome_alone_ms": tl, "batched_mode_over_largest": tm / tl,
+                               "each_outcome_alone_ms": t_each, "sum_of_outcomes_alone_ms": sum(t_each),
                                "max_rel_diff": float(np.max(np.abs(vm - vb) / np.abs(vb)))}
 
     def _multi_gamma():

@@ -66,7 +66,7 @@ lhaf_status grad_plan(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128*
   int occ = 0;
   double best = -1.0;
   J.team = 0;
-  for (int g : {16, 32, 64, 8, 128}) {
+  for (int g : {16, 32, 8}) {  // teams inside one warp (the adjoint's reductions are warp shuffles)
     const size_t smem = ib + (size_t)teams_per_cta(g) * tb;
     if (smem > 227 * 1024) continue;
     const int o = grad_ctas_per_sm(g, smem);

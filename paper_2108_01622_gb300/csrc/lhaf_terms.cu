@@ -242,130 +242,7 @@ __device__ __forceinline__ void build_cta_tables(const TermParams& p, unsigned c
   for (int k = threadIdx.x; k <= p.H + 1; k += CTA) invk[k] = k ? (R)1 / (R)k : (R)0;
 }
 
-// ---------------------------------------------------------------------------------------------
-// Adjoint of one term (reverse mode through Eq. ET_poly). With M = C X, u = v X (X = X_delta'),
-// g_k = Tr(M^k)/(2k) + u M^(k-1) v^T / 2 and f = [t^h] exp(sum g_k t^k), df/dg_k = e_{h-k}:
-//   df/dM = sum_k e_{h-k}/2 (M^(k-1))^T + sum_k e_{h-k}/2 sum_{i+l=k-2} (u M^i)^T (M^l v^T)^T
-//   df/du = sum_k e_{h-k}/2 (M^(k-1) v^T)^T,   df/dv|direct = sum_k e_{h-k}/2 u M^(k-1)
-//   dC = (df/dM) X,   dv = df/dv|direct + (df/du) X
-// The matrix polynomial sum_j c_j M^j (c_j = e_{h-1-j}/2) is evaluated by Horner's rule (dense
-// team matrix products); the second part is a Hankel-weighted sum of outer products of the Krylov
-// vectors x_l = M^l v^T and y_i = u M^i. Ga (n x n) and Gv (n) accumulate weight * (dC, dv).
-// ---------------------------------------------------------------------------------------------
-template <typename R, int G>
-__device__ __forceinline__ void term_adjoint(const typename Cx<R>::t* __restrict__ chat, int nd, int bord, int h,
-                                             const int* delta, const typename Cx<R>::t* e, double weight,
-                                             typename Cx<R>::t* Mb, typename Cx<R>::t* Xa, typename Cx<R>::t* Ta,
-                                             typename Cx<R>::t* Ga, typename Cx<R>::t* Gv, typename Cx<R>::t* xv,
-                                             typename Cx<R>::t* yu, int lt) {
-  using V = typename Cx<R>::t;
-  const int n = nd - bord;
-  const V zero = cmake<V>((R)0, (R)0);
-  const R wr = (R)weight;
-  // M = C X, x_0 = v^T, y_0 = u = v X
-  for (int w = lt; w < n * n; w += G) {
-    const int a = w / n, b = w - a * n;
-    const int dl = delta[b >> 1];
-    const V c = chat[(bord + a) * nd + bord + (b ^ 1)];
-    Mb[w] = cmake<V>(c.x * (R)dl, c.y * (R)dl);
-  }
-  for (int a = lt; a < n; a += G) xv[a] = bord ? chat[(bord + a) * nd] : zero;
-  team_sync<G>();
-  for (int b = lt; b < n; b += G) {
-    const V vb = xv[b ^ 1];
-    const R dl = (R)delta[b >> 1];
-    yu[b] = cmake<V>(vb.x * dl, vb.y * dl);
-  }
-  team_sync<G>();
-  // Krylov vectors x_l = M x_{l-1}, y_l = y_{l-1} M, l = 1..h-1
-  if (bord) {
-    for (int l = 1; l < h; l++) {
-      for (int w = lt; w < 2 * n; w += G) {
-        V acc = zero;
-        if (w < n) {
-          for (int j = 0; j < n; j++) cmac(acc, Mb[w * n + j], xv[(l - 1) * n + j]);
-          xv[l * n + w] = acc;
-        } else {
-          const int c = w - n;
-          for (int i = 0; i < n; i++) cmac(acc, yu[(l - 1) * n + i], Mb[i * n + c]);
-          yu[l * n + c] = acc;
-        }
-      }
-      team_sync<G>();
-    }
-  }
-  // Horner: X = sum_{j<h} c_j M^j, c_j = e_{h-1-j} / 2
-  V* X = Xa;
-  V* T = Ta;
-  {
-    const V c1 = cmake<V>((R)0.5 * e[0].x, (R)0.5 * e[0].y);  // c_{h-1}
-    const V c0 = (h >= 2) ? cmake<V>((R)0.5 * e[1].x, (R)0.5 * e[1].y) : zero;  // c_{h-2}
-    for (int w = lt; w < n * n; w += G) {
-      const int a = w / n, b = w - a * n;
-      V x = zero;
-      if (h >= 2) x = cmul(c1, Mb[w]);
-      if (a == b) {
-        const V d = (h >= 2) ? c0 : c1;
-        x.x += d.x;
-        x.y += d.y;
-      }
-      X[w] = x;
-    }
-    team_sync<G>();
-    for (int j = h - 3; j >= 0; j--) {
-      const V cj = cmake<V>((R)0.5 * e[h - 1 - j].x, (R)0.5 * e[h - 1 - j].y);
-      for (int w = lt; w < n * n; w += G) {
-        const int a = w / n, b = w - a * n;
-        V acc = (a == b) ? cj : zero;
-#pragma unroll 4
-        for (int l = 0; l < n; l++) cmac(acc, Mb[a * n + l], X[l * n + b]);
-        T[w] = acc;
-      }
-      team_sync<G>();
-      V* tmp = X;
-      X = T;
-      T = tmp;
-    }
-  }
-  // Z[i][c] = sum_{l <= h-2-i} e_{h-2-i-l}/2 x_l[c]  (i = 0..h-2), into the free Horner buffer
-  if (bord && h >= 2) {
-    for (int w = lt; w < (h - 1) * n; w += G) {
-      const int i = w / n, c = w - i * n;
-      V acc = zero;
-      for (int l = 0; l <= h - 2 - i; l++) cmac(acc, e[h - 2 - i - l], xv[l * n + c]);
-      T[w] = cmake<V>((R)0.5 * acc.x, (R)0.5 * acc.y);
-    }
-    team_sync<G>();
-  }
-  // accumulate weight * dC and weight * dv
-  for (int w = lt; w < n * n; w += G) {
-    const int a = w / n, b = w - a * n;
-    const int c = b ^ 1;
-    V gm = X[c * n + a];
-    if (bord)
-      for (int i = 0; i <= h - 2; i++) cmac(gm, yu[i * n + a], T[i * n + c]);
-    const R s = wr * (R)delta[b >> 1];
-    V g = Ga[w];
-    g.x = rfma(gm.x, s, g.x);
-    g.y = rfma(gm.y, s, g.y);
-    Ga[w] = g;
-  }
-  if (bord) {
-    for (int b = lt; b < n; b += G) {
-      V dv = zero, du = zero;
-      for (int k = 1; k <= h; k++) {
-        cmac(dv, e[h - k], yu[(k - 1) * n + b]);
-        cmac(du, e[h - k], xv[(k - 1) * n + (b ^ 1)]);
-      }
-      const R dl = (R)delta[b >> 1];
-      V g = Gv[b];
-      g.x = rfma((R)0.5 * wr, rfma(du.x, dl, dv.x), g.x);
-      g.y = rfma((R)0.5 * wr, rfma(du.y, dl, dv.y), g.y);
-      Gv[b] = g;
-    }
-  }
-  team_sync<G>();
-}
+#include "lhaf_adjoint.cuh"
 
 // ---------------------------------------------------------------------------------------------
 // The sieve terms t = p.t_begin + team_global + r * p.total_teams (r < p.rounds, t < p.t_end)
@@ -403,15 +280,22 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
   const V one = cmake<V>((R)1, (R)0);
   double acc_re = 0.0, acc_re_lo = 0.0, acc_im = 0.0, acc_im_lo = 0.0;
 
-  // adjoint buffers (GRAD): X, T (max(n^2, h n) each), Ga (n^2), Gv (n), x_l and y_l (h n each)
+  // adjoint buffers (GRAD, teams of at most one warp): S and Kb (nd x ld each), q_bar
+  // ((nd + 1) x (Hl + 1)), c_bar (nd x Hl), series adjoints (6 x (H + 2)), multipliers and their
+  // adjoints (nd each), pivot rows (nd ints) in shared memory; the gradient sums Ga (n x n) and
+  // Gv (n) in the team's own slice of gpart (global memory: the freed shared memory lets a fourth
+  // team onto an SM at n = 27, measured 34.1 -> 25.9 ms for a 32-photon outcome)
   const int ng = nd - bord;
-  const int nbuf = (ng * ng > h * ng) ? ng * ng : h * ng;
-  V* gX = reinterpret_cast<V*>(reinterpret_cast<unsigned char*>(ts) + ((sizeof(TeamScratch) + 15) & ~(size_t)15));
-  V* gT = gX + nbuf;
-  V* gA = gT + nbuf;
-  V* gV = gA + ng * ng;
-  V* gx = gV + ng;
-  V* gy = gx + h * ng;
+  V* gS = reinterpret_cast<V*>(reinterpret_cast<unsigned char*>(ts) + ((sizeof(TeamScratch) + 15) & ~(size_t)15));
+  V* gK = gS + nd * ld;
+  V* gQ = gK + nd * ld;
+  V* gC = gQ + (nd + 1) * (Hl + 1);
+  V* gSb = gC + nd * Hl;
+  V* gLv = gSb + 6 * (H + 2);
+  V* gLb = gLv + nd;
+  int* gpiv = reinterpret_cast<int*>(gLb + nd);
+  V* gA = GRAD ? gpart + (size_t)team_global * (size_t)(ng * ng + ng) : nullptr;
+  V* gV = GRAD ? gA + ng * ng : nullptr;
   if constexpr (GRAD) {
     for (int w = lt; w < ng * ng + ng; w += G) gA[w] = zero;  // gV follows gA
     team_sync<G>();
@@ -614,6 +498,9 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
         }
       }
       const int r = row;
+      if constexpr (GRAD) {
+        if (lt == 0) gpiv[k] = r;
+      }
       const V ip = crecip(pv);  // issued before the swaps, so its latency overlaps them
       if (STAGE && p.ng > 0 && ld > nd && lt == 0) W[k * ld + nd].x = (R)r;  // for the loop vectors
       // swap rows r and k+1 (columns k..nd-1), then columns r and k+1: a similarity transform
@@ -725,7 +612,7 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
         // characteristic polynomial (they are R_{k+1} of the bordered form).
         // Two vectors per pass (nv = 2, or 1 for the last of an odd count): the swaps and
         // multipliers, and each H entry of the products, are loaded once for both.
-        V* xu = gX;           // u' of the pass's vectors, nd each
+        V* xu = gS;           // u' of the pass's vectors, nd each
         V* xa = xu + 2 * nd;  // Krylov vectors
         V* xb = xa + 2 * nd;  // next Krylov vectors
         const V* gvs = reinterpret_cast<const V*>(p.gv);
@@ -841,6 +728,11 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
           team_sync<G>();
         }
       }
+    }
+
+    if constexpr (GRAD) {  // the Hessenberg form with its multipliers, for the adjoint
+      for (int w = lt; w < nd * ld; w += G) gS[w] = W[w];
+      team_sync<G>();
     }
 
     // ---- La Budde's recurrence, reverse (trailing blocks), truncated at degree Hl ----
@@ -1060,14 +952,13 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
       }
       team_sync<G>();
       if constexpr (GRAD) {
-        term_adjoint<R, G>(chat, nd, bord, h, ts->delta, Se, ts->weight, W, gX, gT, gA, gV, gx, gy, lt);
+        adjoint_series_labudde<R, G>(W, gS, gK, gQ, gC, gSb, Sa, Sc, SR, Sp, Sz, Se, nd, ld, bord, h, H, Hl, lt);
+        adjoint_elimination<R, G>(gS, gK, gLv, gLb, gpiv, nd, ld, lt);
+        adjoint_accumulate<R, G>(gK, nd, ld, bord, ts->delta, ts->weight, gA, gV, lt);
       }
     }
   }
-  if constexpr (GRAD) {
-    V* o = gpart + (size_t)team_global * (size_t)(ng * ng + ng);
-    for (int w = lt; w < ng * ng + ng; w += G) o[w] = gA[w];
-  }
+
 
   acc[0] = acc_re;
   acc[1] = acc_re_lo;
@@ -1947,22 +1838,24 @@ cudaError_t launch_item_finalize(const double* acc, const int* item_h, int n_ite
 size_t cta_table_bytes(bool fp32, int Hl, int H) { return items_bytes_of(fp32, Hl, H); }
 
 size_t grad_team_bytes(int nd, int H, int h, int bord) {
-  const int n = nd - bord;
-  const size_t nbuf = (size_t)((n * n > h * n) ? n * n : h * n);
+  (void)h;
+  const int n = nd - bord, ld = nd | 1, Hl = H < nd ? H : nd;
   size_t b = team_shared_bytes(false, nd, H, 0, false) + ((sizeof(TeamScratch) + 15) & ~(size_t)15);
-  b += (2 * nbuf + (size_t)n * n + n + 2 * (size_t)h * n) * sizeof(double2);
+  (void)n;
+  b += (2 * (size_t)nd * ld + (size_t)(nd + 1) * (Hl + 1) + (size_t)nd * Hl + 6 * (size_t)(H + 2) + 2 * (size_t)nd) *
+       sizeof(double2);
+  b += (size_t)nd * sizeof(int);
   return (b + 15) & ~(size_t)15;
 }
 
 template <int G> static const void* gptr() { return (const void*)grad_kernel<G>; }
 
+// The adjoint's reductions run inside one warp: teams of 8, 16 or 32 lanes.
 static const void* pick_grad(int team) {
   switch (team) {
     case 8: return gptr<8>();
     case 16: return gptr<16>();
     case 32: return gptr<32>();
-    case 64: return gptr<64>();
-    case 128: return gptr<128>();
   }
   return nullptr;
 }
