@@ -88,7 +88,7 @@ extern "C" lhaf_status lhaf_batched_mode(lhaf_ctx* ctx, int M, const lhaf_c128* 
     return LHAF_ENOMEM;
   uint64_t terms_all = 0, h2d = sizeof(int) * (uint64_t)n_out_all;
   double flops_all = 0.0;
-  int launches = 0, team_used = 0, nd_max = 0;
+  int launches = 0, team_used = 0, nd_max_all = 0;
 
   // host staging of the per-class tables: [coefficients | outcome degrees | segments] per class
   struct ClassRun {
@@ -275,40 +275,95 @@ extern "C" lhaf_status lhaf_batched_mode(lhaf_ctx* ctx, int M, const lhaf_c128* 
       cudaMemcpyAsync(w.item_h.p, w.h_item_h.p, sizeof(int) * n_out_all, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return (lhaf_status)record_cuda(cudaPeekAtLastError(), "batched-mode setup");
   if (stats) cudaEventRecord(ctx->ev0, s);
-  for (const ClassRun& cr : runs) {
-    const Plan& pl = cr.pl;
-    const int A = cr.A;
-    const int n_out = (int)cr.outs.size();
-    // the previous uploads read the pinned buffers (slot matrix, tables) rewritten below
+  // One parity class at a time: the slot matrices of all its sieves (zero-digit groups) in one
+  // pool, one chunk queue over all of them (grouped launches, largest working dimension first,
+  // chunks never straddle two sieves), the series of every staged column, one segment per outcome.
+  for (int cls = 0; cls < 2; cls++) {
+    std::vector<int> members;
+    for (int ri = 0; ri < (int)runs.size(); ri++)
+      if ((runs[ri].outs[0] & 1) == cls) members.push_back(ri);
+    if (members.empty()) continue;
+    std::stable_sort(members.begin(), members.end(),
+                     [&](int a, int b) { return runs[a].pl.nd > runs[b].pl.nd; });
+    const ClassRun& c0 = runs[members[0]];
+    const int A = c0.A, n_out = (int)c0.outs.size();
+    const int h = c0.pl.h, bord = c0.pl.bord, H = c0.pl.H;
+    const int nj = (int)members.size();
+    // the previous class's uploads read the pinned buffers rewritten below
     if (cudaEventRecord(w.uploaded, s) != cudaSuccess || cudaEventSynchronize(w.uploaded) != cudaSuccess)
       return (lhaf_status)record_cuda(cudaPeekAtLastError(), "batched-mode upload wait");
-    // slot matrix
-    build_chat_host(pl, M, B, gamma, (std::complex<double>*)ctx->h_chat);
-    if (cudaMemcpyAsync(ctx->d_chat, ctx->h_chat, sizeof(double2) * pl.nd * pl.nd, cudaMemcpyHostToDevice, s) !=
-        cudaSuccess)
-      return (lhaf_status)record_cuda(cudaPeekAtLastError(), "batched-mode slot matrix");
-    h2d += sizeof(double2) * (uint64_t)pl.nd * pl.nd;
-    // staging: rows of every term, its weight and its self delta' (second weight row)
-    const int rows = pl.bord ? 2 * pl.h + 1 : pl.h;
+    long long pool = 0;
+    for (int ri : members) pool += (long long)runs[ri].pl.nd * runs[ri].pl.nd;
+    if (!w.h_items.reserve(sizeof(BatchItem) * nj) || !w.items.reserve(sizeof(BatchItem) * nj) ||
+        !w.h_chat.reserve(sizeof(double2) * pool) || !w.chat.reserve(sizeof(double2) * pool) ||
+        !w.counter.reserve(sizeof(unsigned long long)))
+      return LHAF_ENOMEM;
+    BatchItem* jobs = static_cast<BatchItem*>(w.h_items.p);
+    std::memset(jobs, 0, sizeof(BatchItem) * nj);
+    std::complex<double>* hc = static_cast<std::complex<double>*>(w.h_chat.p);
+    int nd_max = 0, P_max = 0, Hl_max = 0, rep = 0;
+    double cost_max = -1.0;
+    long long off = 0;
+    for (int j = 0; j < nj; j++) {
+      const ClassRun& cr = runs[members[j]];
+      const Plan& g = cr.pl;
+      fill_params(g, false, true, 32, flags, jobs[j].p);
+      jobs[j].p.bq = cr.bq;
+      jobs[j].p.bA = A;
+      jobs[j].p.t_end = g.T;  // the sieve's term count (the kernel sets the per-chunk range)
+      jobs[j].chat_off = off;
+      for (int q = 0; q < kMaxDim; q++) jobs[j].slot_mode[q] = q < 2 * g.P ? g.slot_mode[q] : -1;
+      build_chat_host(g, M, B, gamma, hc + off);
+      off += (long long)g.nd * g.nd;
+      nd_max = std::max(nd_max, g.nd);
+      P_max = std::max(P_max, g.P);
+      Hl_max = std::max(Hl_max, g.Hl);
+      const double c = lhaf_model_flops_per_term(g.nd, g.h, g.bord) * (double)g.T;
+      if (c > cost_max) {
+        cost_max = c;
+        rep = j;
+      }
+    }
+    if (cudaMemcpyAsync(w.items.p, jobs, sizeof(BatchItem) * nj, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(w.chat.p, hc, sizeof(double2) * pool, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return (lhaf_status)record_cuda(cudaPeekAtLastError(), "batched-mode sieves");
+    h2d += sizeof(BatchItem) * (uint64_t)nj + sizeof(double2) * (uint64_t)pool;
+    // staging first (the tuner's staged trial writes into it): coefficient rows of every term, its
+    // weight and its self delta' (second weight row), at most 256 MB of rows per launch
+    const int rows = bord ? 2 * h + 1 : h;
+    uint64_t T_class = 0;
+    for (int ri : members) T_class += runs[ri].pl.T;
     uint64_t cap = ((size_t)256 << 20) / ((size_t)rows * sizeof(double2));
     cap = std::min<uint64_t>(cap, (uint64_t)ctx->partial_cap * 64);
-    cap = std::min<uint64_t>(cap, std::max<uint64_t>(pl.T, 64));
+    cap = std::min<uint64_t>(cap, T_class + 32ull * (uint64_t)nj);  // every term plus chunk padding
+    cap = std::max<uint64_t>(cap, 32);
     if (!ensure_stage(ctx, (size_t)rows * sizeof(double2) * cap, 2 * cap)) return LHAF_ENOMEM;
+    // team size on the costliest sieve, the class's shared memory and occupancy
     int occ = 0;
-    const int team = pick_team(ctx, false, pl, true, 4, ctx->d_chat, &occ);
+    const double2* rep_chat = static_cast<const double2*>(w.chat.p) + jobs[rep].chat_off;
+    const int team = pick_team(ctx, false, runs[members[rep]].pl, true, 4, rep_chat, &occ);
     if (team == 0) return LHAF_ETOOBIG;
-    occ = ctas_per_sm_override(occ);
+    const int tpc = teams_per_cta(team);
+    const size_t team_bytes = team_shared_bytes(false, nd_max, H, P_max, true);
+    const size_t items_bytes = cta_table_bytes(false, Hl_max, H);
+    const size_t smem = items_bytes + (size_t)tpc * team_bytes;
+    if (smem > 227 * 1024) return LHAF_ETOOBIG;
+    const int occ_g = grouped_ctas_per_sm(false, team, smem, true);
+    if (occ_g <= 0) return LHAF_ETOOBIG;
+    occ = ctas_per_sm_override(std::min(occ > 0 ? occ : occ_g, occ_g));
     team_used = std::max(team_used, team);
-    nd_max = std::max(nd_max, pl.nd);
-    TermParams p;
-    fill_params(pl, false, true, team, flags, p);
-    p.bq = cr.bq;
-    p.bA = A;
-    // outcome tables: degrees and coefficients (delta' = -A..A)
+    nd_max_all = std::max(nd_max_all, nd_max);
+    // chunks of tpc terms per sieve
+    std::vector<long long> chunk_off(nj + 1, 0);
+    for (int j = 0; j < nj; j++)
+      chunk_off[j + 1] = chunk_off[j] + (long long)((runs[members[j]].pl.T + tpc - 1) / tpc);
+    const long long n_chunks = chunk_off[nj];
+    const long long span = std::max<long long>(1, (long long)(cap / tpc));  // chunks per launch
+    // outcome tables: coefficients (delta' = -A..A) and degrees, after the chunk offsets
     std::vector<int> h_out(n_out);
     std::vector<double> coef((size_t)n_out * (2 * A + 1), 0.0);
     for (int t = 0; t < n_out; t++) {
-      const int n = cr.outs[t], a = n / 2;
+      const int n = c0.outs[t], a = n / 2;
       h_out[t] = (N_fixed + n + 1) / 2;
       for (int dl = -A; dl <= A; dl++) {
         if (std::abs(dl) > a || ((a - dl) & 1)) continue;
@@ -316,30 +371,31 @@ extern "C" lhaf_status lhaf_batched_mode(lhaf_ctx* ctx, int M, const lhaf_c128* 
         coef[(size_t)t * (2 * A + 1) + (dl + A)] = ((k & 1) ? -1.0 : 1.0) * binom_host(a, k);
       }
     }
-    // chunks and their segments (one per outcome: its blocks' partials)
-    const uint64_t T = pl.T;
-    const uint64_t n_chunks = (T + cap - 1) / cap;
+    // per launch: the segments of its blocks (one per outcome)
     std::vector<long long> segb;
     std::vector<int> segi;
-    std::vector<long long> sb_off(n_chunks), si_off(n_chunks);
-    for (uint64_t ck = 0; ck < n_chunks; ck++) {
-      const uint64_t nn = std::min<uint64_t>(T, (ck + 1) * cap) - ck * cap;
-      const long long blocks = series_blocks((long long)nn);
-      sb_off[ck] = (long long)segb.size();
-      si_off[ck] = (long long)segi.size();
+    std::vector<long long> sb_off, si_off;
+    for (long long k0 = 0; k0 < n_chunks; k0 += span) {
+      const long long nn = (std::min(n_chunks, k0 + span) - k0) * tpc;
+      const long long blocks = series_blocks(nn);
+      sb_off.push_back((long long)segb.size());
+      si_off.push_back((long long)segi.size());
       for (int t = 0; t <= n_out; t++) segb.push_back((long long)t * blocks);
-      for (int t = 0; t < n_out; t++) segi.push_back(cr.outs[t]);
+      for (int t = 0; t < n_out; t++) segi.push_back(c0.outs[t]);
     }
-    const size_t tab_bytes = sizeof(int) * h_out.size() + sizeof(double) * coef.size();
+    const size_t tab_bytes =
+        sizeof(long long) * (nj + 1) + sizeof(double) * coef.size() + sizeof(int) * h_out.size();
     if (!w.h_chunks.reserve(tab_bytes + 16) || !w.chunks.reserve(tab_bytes + 16) ||
-        !w.h_seg_begin.reserve(sizeof(long long) * segb.size()) || !w.seg_begin.reserve(sizeof(long long) * segb.size()) ||
-        !w.h_seg_item.reserve(sizeof(int) * segi.size()) || !w.seg_item.reserve(sizeof(int) * segi.size()) ||
-        !w.entries.reserve(4 * sizeof(double) * (size_t)n_out * (size_t)series_blocks((long long)cap)))
+        !w.h_seg_begin.reserve(sizeof(long long) * segb.size()) ||
+        !w.seg_begin.reserve(sizeof(long long) * segb.size()) || !w.h_seg_item.reserve(sizeof(int) * segi.size()) ||
+        !w.seg_item.reserve(sizeof(int) * segi.size()) ||
+        !w.entries.reserve(4 * sizeof(double) * (size_t)n_out * (size_t)series_blocks((long long)(span * tpc))))
       return LHAF_ENOMEM;
-    // coefficient table first (8-byte aligned), then the outcome degrees
     char* ht = static_cast<char*>(w.h_chunks.p);
-    std::memcpy(ht, coef.data(), sizeof(double) * coef.size());
-    std::memcpy(ht + sizeof(double) * coef.size(), h_out.data(), sizeof(int) * h_out.size());
+    std::memcpy(ht, chunk_off.data(), sizeof(long long) * (nj + 1));
+    std::memcpy(ht + sizeof(long long) * (nj + 1), coef.data(), sizeof(double) * coef.size());
+    std::memcpy(ht + sizeof(long long) * (nj + 1) + sizeof(double) * coef.size(), h_out.data(),
+                sizeof(int) * h_out.size());
     std::memcpy(w.h_seg_begin.p, segb.data(), sizeof(long long) * segb.size());
     std::memcpy(w.h_seg_item.p, segi.data(), sizeof(int) * segi.size());
     if (cudaMemcpyAsync(w.chunks.p, w.h_chunks.p, tab_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -349,32 +405,38 @@ extern "C" lhaf_status lhaf_batched_mode(lhaf_ctx* ctx, int M, const lhaf_c128* 
             cudaSuccess)
       return (lhaf_status)record_cuda(cudaPeekAtLastError(), "batched-mode tables");
     h2d += tab_bytes + sizeof(long long) * segb.size() + sizeof(int) * segi.size();
-    const double* d_coef = static_cast<const double*>(w.chunks.p);
-    const int* d_hout = reinterpret_cast<const int*>(static_cast<const char*>(w.chunks.p) + sizeof(double) * coef.size());
-    const int tpc = teams_per_cta(team);
+    const long long* d_chunks = static_cast<const long long*>(w.chunks.p);
+    const double* d_coef = reinterpret_cast<const double*>(static_cast<const char*>(w.chunks.p) +
+                                                           sizeof(long long) * (nj + 1));
+    const int* d_hout = reinterpret_cast<const int*>(static_cast<const char*>(w.chunks.p) +
+                                                     sizeof(long long) * (nj + 1) + sizeof(double) * coef.size());
     const uint64_t max_ctas = (uint64_t)ctx->sms * (uint64_t)std::max(occ, 1);
-    for (uint64_t ck = 0; ck < n_chunks; ck++) {
-      const uint64_t t0 = ck * cap, t1 = std::min<uint64_t>(T, t0 + cap), nn = t1 - t0;
+    int li = 0;
+    for (long long k0 = 0; k0 < n_chunks; k0 += span, li++) {
+      const long long k1 = std::min(n_chunks, k0 + span);
+      const long long nn = (k1 - k0) * tpc;  // staged columns of this launch (padding included)
       unsigned long long rounds = 1;
-      const uint64_t grid = balanced_grid(nn, tpc, max_ctas, &rounds);
-      p.total_teams = grid * (uint64_t)tpc;
-      p.rounds = rounds;
-      p.t_begin = t0;
-      p.t_end = t1;
-      cudaError_t e = launch_terms(false, team, ctx->d_chat, p, (int)grid, ctx->d_partials, s, ctx->d_stage,
-                                   ctx->d_wstage, (long long)cap);
+      const uint64_t grid = balanced_grid((uint64_t)(k1 - k0), 1, max_ctas, &rounds);
+      if (cudaMemsetAsync(w.counter.p, 0, sizeof(unsigned long long), s) != cudaSuccess)
+        return (lhaf_status)record_cuda(cudaPeekAtLastError(), "chunk queue reset");
+      cudaError_t e = launch_grouped_terms(false, team, w.chat.p, (const BatchItem*)w.items.p, nj, d_chunks, k0, k1,
+                                           (int)grid, (int)rounds, 0ull, ~0ull, (int)team_bytes, (int)items_bytes,
+                                           ctx->d_partials, ctx->d_stage, ctx->d_wstage, (long long)cap, s, 0,
+                                           (unsigned long long*)w.counter.p);
       if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "batched-mode terms kernel");
-      e = launch_series_modes(false, ctx->d_stage, ctx->d_wstage, (long long)nn, (long long)cap, pl.h, pl.bord, n_out,
-                              d_hout, d_coef, A, (double*)w.entries.p, s);
+      e = launch_series_modes(false, ctx->d_stage, ctx->d_wstage, nn, (long long)cap, h, bord, n_out, d_hout, d_coef,
+                              A, (double*)w.entries.p, s);
       if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "batched-mode series kernel");
-      e = launch_segment_reduce((const double*)w.entries.p, (const long long*)w.seg_begin.p + sb_off[ck],
-                                (const int*)w.seg_item.p + si_off[ck], n_out, (flags & LHAF_PLAIN_ACCUM) ? 1 : 0,
+      e = launch_segment_reduce((const double*)w.entries.p, (const long long*)w.seg_begin.p + sb_off[li],
+                                (const int*)w.seg_item.p + si_off[li], n_out, (flags & LHAF_PLAIN_ACCUM) ? 1 : 0,
                                 (double*)w.acc.p, s);
       if (e != cudaSuccess) return (lhaf_status)record_cuda(e, "batched-mode reduction");
       launches += 3;
     }
-    terms_all += T;
-    flops_all += (double)T * lhaf_model_flops_per_term(pl.nd, pl.h, pl.bord);
+    for (int ri : members) {
+      terms_all += runs[ri].pl.T;
+      flops_all += (double)runs[ri].pl.T * lhaf_model_flops_per_term(runs[ri].pl.nd, runs[ri].pl.h, runs[ri].pl.bord);
+    }
   }
   if (launch_item_finalize((const double*)w.acc.p, (const int*)w.item_h.p, n_out_all, (double2*)w.out.p, s) !=
       cudaSuccess)
@@ -392,7 +454,7 @@ extern "C" lhaf_status lhaf_batched_mode(lhaf_ctx* ctx, int M, const lhaf_c128* 
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     stats->kernel_ms = ms;
     stats->terms = terms_all;
-    stats->n_dim = nd_max;
+    stats->n_dim = nd_max_all;
     stats->h = (N_fixed + n_cut + 1) / 2;
     stats->pairs = (int32_t)runs.size();
     stats->team = team_used;
