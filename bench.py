@@ -547,18 +547,20 @@ def run_extras(ctx, torch, dev, lg, workload):
                                "max_rel_diff": float(np.max(np.abs(vm - vb) / np.abs(vb)))}
 
     def _multi_gamma():
-        # several loop-weight vectors on one pattern (App. B.5, threshold sub-detectors): 16 vectors on
-        # the 40-photon collision pattern, against the same 16 loop hafnians as one batch
+        # several loop-weight vectors on one pattern (App. B.5, threshold sub-detectors): 4, 16 and 64
+        # vectors on the 40-photon collision pattern, each against the same loop hafnians as one batch
         pm_ = wl.collision_lhaf_40(seed=2)
-        Gm = wl.complex_normal(np.random.default_rng(21), (16, len(pm_.reps)))
-        Rm = np.repeat(np.asarray(pm_.reps)[None, :], 16, axis=0)
-        vm_ = ctx.lhaf_multi_gamma(pm_.B, Gm, pm_.reps)
-        vb_, _ = ctx.lhaf_batched(pm_.B, Gm, Rm)
-        tmg = _timed(torch, lambda: ctx.lhaf_multi_gamma(pm_.B, Gm, pm_.reps), reps=3)
-        tbg = _timed(torch, lambda: ctx.lhaf_batched(pm_.B, Gm, Rm), reps=3)
-        out["multi_gamma"] = {"workload": "16 loop-weight vectors on the 40-photon collision pattern (100-mode Haar)",
-                              "multi_gamma_ms": tmg, "batched_ms": tbg, "speedup": tbg / tmg,
-                              "max_rel_diff": float(np.max(np.abs(vm_ - vb_) / np.abs(vb_)))}
+        res = {"workload": "4, 16 and 64 loop-weight vectors on the 40-photon collision pattern (100-mode Haar)"}
+        for ng in (4, 16, 64):
+            Gm = wl.complex_normal(np.random.default_rng(21), (ng, len(pm_.reps)))
+            Rm = np.repeat(np.asarray(pm_.reps)[None, :], ng, axis=0)
+            vm_ = ctx.lhaf_multi_gamma(pm_.B, Gm, pm_.reps)
+            vb_, _ = ctx.lhaf_batched(pm_.B, Gm, Rm)
+            tmg = _timed(torch, lambda: ctx.lhaf_multi_gamma(pm_.B, Gm, pm_.reps), reps=3)
+            tbg = _timed(torch, lambda: ctx.lhaf_batched(pm_.B, Gm, Rm), reps=3)
+            res[str(ng)] = {"multi_gamma_ms": tmg, "batched_ms": tbg, "speedup": tbg / tmg,
+                            "max_rel_diff": float(np.max(np.abs(vm_ - vb_) / np.abs(vb_)))}
+        out["multi_gamma"] = res
 
     def _chain_rule_step():
         # one chain-rule step (App. A.2): a 50-mode pure state, 20 photons sampled on half of the

@@ -226,8 +226,11 @@ lhaf_status lhaf_batched_mode(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lh
  *   out: HOST n_gamma; stats: HOST or NULL. 1 <= n_gamma <= 256. flags: LHAF_PLAIN_ACCUM,
  *   LHAF_NO_REPEAT_SPEEDUP. Errors: LHAF_EINVAL for bad arguments (NULL, non-finite entries of the
  *   occupied modes, negative reps, other flags), LHAF_ETOOBIG when ceil(N/2) > 24 (the staged series
- *   limit) or the working dimension exceeds LHAF_MAX_DIM, LHAF_ECUDA / LHAF_ENOMEM as for lhaf(). The middle digits of even-eta pairs
- *   are evaluated on the full working matrix (no zero-digit groups). Synchronous. */
+ *   limit) or the working dimension exceeds LHAF_MAX_DIM, LHAF_ECUDA / LHAF_ENOMEM as for lhaf(). The middle
+ *   digits of even-eta pairs are evaluated on the full working matrix (no zero-digit groups); a
+ *   pattern that has such digits with fewer than 16 vectors runs as lhaf_batched of the pattern
+ *   repeated instead (the batch's zero-digit groups are worth more than sharing among few vectors;
+ *   an item error is then returned as the call's status). Synchronous. */
 lhaf_status lhaf_multi_gamma(lhaf_ctx* ctx, int M, const lhaf_c128* B, int n_gamma, const lhaf_c128* gammas,
                              const int32_t* reps, uint32_t flags, lhaf_c128* out, lhaf_stats* stats);
 

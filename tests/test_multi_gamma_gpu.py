@@ -97,3 +97,15 @@ def test_multi_gamma_vector_count_limit(ctx, lg):
     with pytest.raises(lg.LhafError) as e:
         ctx.lhaf_multi_gamma(p.B, np.ones((257, 4), complex), [1, 1, 0, 1])
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("n_gamma", [4, 16, 24])
+def test_multi_gamma_both_paths_on_even_repeats(ctx, lg, n_gamma):
+    # a pattern with zero-digit groups: fewer than 16 vectors run as a batch of single loop
+    # hafnians, 16 and more share each term's reduction; both against the oracle
+    reps = (2, 2, 2, 2, 1, 1)
+    p = wl.small_problem(seed=13, M=len(reps), reps=reps, loops=True)
+    G = wl.complex_normal(np.random.default_rng(n_gamma), (n_gamma, len(reps)))
+    out = ctx.lhaf_multi_gamma(p.B, G, list(reps))
+    for g in (0, n_gamma // 2, n_gamma - 1):
+        assert rel(out[g], lo.lhaf_repeated(p.B, G[g], np.array(reps))) < TOL
