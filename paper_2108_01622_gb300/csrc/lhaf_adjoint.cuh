@@ -25,7 +25,8 @@
 // Team-local storage of the adjoint (all in shared memory, complex of type V):
 //   S  nd x ld : the Hessenberg form with the multipliers (copied before La Budde), then the state
 //   Kb nd x ld : the adjoint of the state
-//   Qb (nd + 1) x (Hl + 1) : q_bar;  Cb nd x Hl : c_bar_jl at [j][l - j - 1]
+//   Qb (Hl + 1) x (Hl + 1) : q_bar, a window of rows j .. j + Hl (row r in slot r mod (Hl + 1));
+//   Cb nd x Hl : c_bar_jl at [j][l - j - 1]
 //   Sb 6 x (H + 2) : e_bar, z_bar, p_bar, R_bar, a_bar, c_bar (series)
 //   Lv, Lb nd each : the step's multipliers and their adjoints
 //   piv nd ints : the pivot rows r_k
@@ -57,7 +58,7 @@ __device__ __forceinline__ void adjoint_series_labudde(const typename Cx<R>::t* 
   V* cb = ab + (H + 2);
   for (int x = lt; x < 6 * (H + 2); x += G) Sb[x] = zero;
   for (int x = lt; x < nd * ld; x += G) Kb[x] = zero;
-  for (int x = lt; x < (nd + 1) * (Hl + 1); x += G) Qb[x] = zero;
+  for (int x = lt; x < (Hl + 1) * (Hl + 1); x += G) Qb[x] = zero;
   team_sync<G>();
   if (lt == 0) eb[h] = cmake<V>((R)1, (R)0);
   team_sync<G>();
@@ -126,16 +127,18 @@ __device__ __forceinline__ void adjoint_series_labudde(const typename Cx<R>::t* 
     }
   }
   team_sync<G>();
-  // La Budde backwards: j = 0, 1, ..., nd - 1 (q_bar_j is complete when j is reached)
+  // La Budde backwards: j = 0, 1, ..., nd - 1 (q_bar_j is complete when j is reached; step j
+  // writes rows j+1 .. j+Hl of the window, and row j's slot is cleared for row j + Hl + 1)
+  const int QW = Hl + 1;
   for (int j = 0; j < nd; j++) {
     const int degj = min(Hl, nd - j);
     const int nl = min(Hl - 1, nd - 1 - j);  // l = j+1 .. j+nl, d = l - j + 1 <= Hl
-    const V* qbj = Qb + j * (Hl + 1);
+    V* qbj = Qb + (j % QW) * QW;
     for (int x = lt; x <= nl; x += G) {
       if (x < nl) {
         const int l = j + 1 + x, d = x + 2;
         const V c = W[j * ld + l];  // c_jl (La Budde's table over H)
-        V* qbl = Qb + (l + 1) * (Hl + 1);
+        V* qbl = Qb + ((l + 1) % QW) * QW;
         const int mmax = min(Hl - d, nd - l - 1);
         V s = zero;
         for (int mp = 0; mp <= mmax; mp++) {
@@ -148,7 +151,7 @@ __device__ __forceinline__ void adjoint_series_labudde(const typename Cx<R>::t* 
         Cb[j * Hl + x] = cmake<V>(-s.x, -s.y);
       } else {
         const V hjj = S[j * ld + j];
-        V* qb1 = Qb + (j + 1) * (Hl + 1);
+        V* qb1 = Qb + ((j + 1) % QW) * QW;
         V s = zero;
         for (int m = 0; m <= degj; m++) {
           const V g = qbj[m];
@@ -164,6 +167,8 @@ __device__ __forceinline__ void adjoint_series_labudde(const typename Cx<R>::t* 
         Kb[j * ld + j] = cmake<V>(-s.x, -s.y);
       }
     }
+    team_sync<G>();
+    for (int m = lt; m < QW; m += G) qbj[m] = zero;  // row j is done: its slot serves row j + QW
     team_sync<G>();
   }
   // c_jl = h_jl P_j(l), P_j(l) = prod_(r=j+1..l) h_(r,r-1): h_bar_jl += c_bar_jl P_j(l) (lane per

@@ -281,7 +281,7 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
   double acc_re = 0.0, acc_re_lo = 0.0, acc_im = 0.0, acc_im_lo = 0.0;
 
   // adjoint buffers (GRAD, teams of at most one warp): S and Kb (nd x ld each), q_bar
-  // ((nd + 1) x (Hl + 1)), c_bar (nd x Hl), series adjoints (6 x (H + 2)), multipliers and their
+  // ((Hl + 1) x (Hl + 1) window), c_bar (nd x Hl), series adjoints (6 x (H + 2)), multipliers and their
   // adjoints (nd each), pivot rows (nd ints) in shared memory; the gradient sums Ga (n x n) and
   // Gv (n) in the team's own slice of gpart (global memory: the freed shared memory lets a fourth
   // team onto an SM at n = 27, measured 34.1 -> 25.9 ms for a 32-photon outcome)
@@ -289,7 +289,7 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
   V* gS = reinterpret_cast<V*>(reinterpret_cast<unsigned char*>(ts) + ((sizeof(TeamScratch) + 15) & ~(size_t)15));
   V* gK = gS + nd * ld;
   V* gQ = gK + nd * ld;
-  V* gC = gQ + (nd + 1) * (Hl + 1);
+  V* gC = gQ + (Hl + 1) * (Hl + 1);
   V* gSb = gC + nd * Hl;
   V* gLv = gSb + 6 * (H + 2);
   V* gLb = gLv + nd;
@@ -1840,9 +1840,11 @@ size_t cta_table_bytes(bool fp32, int Hl, int H) { return items_bytes_of(fp32, H
 size_t grad_team_bytes(int nd, int H, int h, int bord) {
   (void)h;
   const int n = nd - bord, ld = nd | 1, Hl = H < nd ? H : nd;
-  size_t b = team_shared_bytes(false, nd, H, 0, false) + ((sizeof(TeamScratch) + 15) & ~(size_t)15);
+  // team_shared_bytes covers the working matrix, the series arrays and the team scratch (ending
+  // 16-byte aligned, where the adjoint's buffers start)
+  size_t b = team_shared_bytes(false, nd, H, 0, false);
   (void)n;
-  b += (2 * (size_t)nd * ld + (size_t)(nd + 1) * (Hl + 1) + (size_t)nd * Hl + 6 * (size_t)(H + 2) + 2 * (size_t)nd) *
+  b += (2 * (size_t)nd * ld + (size_t)(Hl + 1) * (Hl + 1) + (size_t)nd * Hl + 6 * (size_t)(H + 2) + 2 * (size_t)nd) *
        sizeof(double2);
   b += (size_t)nd * sizeof(int);
   return (b + 15) & ~(size_t)15;
