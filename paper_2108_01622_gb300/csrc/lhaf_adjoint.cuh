@@ -22,14 +22,25 @@
 // for a matrix polynomial.
 #pragma once
 
-// Team-local storage of the adjoint (all in shared memory, complex of type V):
+// FP64 instructions issue per warp whatever the number of active lanes (an SM retires about one
+// FP64 warp instruction per 16 cycles), so every phase below spreads its multiply-adds evenly over
+// the team's lanes: element-wise updates as flat item lists, sums through team_dots.
+//
+// Team-local storage of the adjoint (shared memory, complex of type V):
 //   S  nd x ld : the Hessenberg form with the multipliers (copied before La Budde), then the state
 //   Kb nd x ld : the adjoint of the state
-//   Qb (Hl + 1) x (Hl + 1) : q_bar, a window of rows j .. j + Hl (row r in slot r mod (Hl + 1));
-//   Cb nd x Hl : c_bar_jl at [j][l - j - 1]
-//   Sb 6 x (H + 2) : e_bar, z_bar, p_bar, R_bar, a_bar, c_bar (series)
-//   Lv, Lb nd each : the step's multipliers and their adjoints
+//   Qb (nd + 1) x (Hl + 1) : q_bar_j in row j; then P_j(l - 1) for the product rule (nd x Hl)
+//   U  adjoint_union entries, reused by phase: the series adjoints (6 x (H + 2)); then c_bar_jl at
+//      [j * Hl + l - j - 1] (nd x Hl); then the multipliers l, their adjoints l_bar (nd each) and
+//      the partial sums of team_dots (dots_slots(G))
 //   piv nd ints : the pivot rows r_k
+__host__ __device__ constexpr int dots_np(int G) { return 2 + (kMaxDim + G - 1) / G; }
+__host__ __device__ constexpr int dots_slots(int G) { return G * dots_np(G); }
+__host__ __device__ constexpr int adjoint_union(int nd, int H, int Hl, int G) {
+  return (nd * Hl > 6 * (H + 2) ? (nd * Hl > 2 * nd + dots_slots(G) ? nd * Hl : 2 * nd + dots_slots(G))
+                                : (6 * (H + 2) > 2 * nd + dots_slots(G) ? 6 * (H + 2) : 2 * nd + dots_slots(G)));
+}
+
 template <typename V>
 __device__ __forceinline__ V q_fwd(const V* W, int ld, int nd, int l, int m) {
   // forward q_l[m] as La Budde left it: q_l[0] = 1, q_l[m] at W[l + m - 1][l] (1 <= m <= nd - l)
@@ -38,27 +49,75 @@ __device__ __forceinline__ V q_fwd(const V* W, int ld, int nd, int l, int m) {
   return W[(l + m - 1) * ld + l];
 }
 
+// Sums out_o = sum_(q < len) x_oq y_oq for o < no (no <= kMaxDim), with the no * len products cut
+// into equal contiguous ranges, one per lane. A lane's range meets at most dots_np(G) outputs; its
+// partial sums go to part[lt * dots_np(G) + u]. After a team barrier, lane per output adds the
+// partials of the lanes whose ranges met it and passes the sum to done(o, sum).
+// prod(o, q, x, y) loads the factors of product q of output o.
+template <typename R, int G, typename Prod, typename Done>
+__device__ __forceinline__ void team_dots(int no, int len, typename Cx<R>::t* part, int lt, Prod prod, Done done) {
+  using V = typename Cx<R>::t;
+  constexpr int NP = dots_np(G);
+  const int F = no * len;
+  const int c = (F + G - 1) / G;
+  int f = lt * c;
+  const int fe = min(f + c, F);
+  if (f < fe) {
+    int o = f / len, q = f - o * len, u = 0;
+    V s = cmake<V>((R)0, (R)0);
+    for (; f < fe; f++) {
+      V x, y;
+      prod(o, q, x, y);
+      cmac(s, x, y);
+      if (++q == len) {
+        part[lt * NP + u] = s;
+        u++;
+        s = cmake<V>((R)0, (R)0);
+        q = 0;
+        o++;
+      }
+    }
+    if (q != 0) part[lt * NP + u] = s;
+  }
+  team_sync<G>();
+  for (int oo = lt; oo < no; oo += G) {
+    V t = cmake<V>((R)0, (R)0);
+    if (len > 0) {
+      const int l0 = (oo * len) / c, l1 = ((oo + 1) * len - 1) / c;
+      t = part[l0 * NP + (oo - (l0 * c) / len)];
+      for (int l = l0 + 1; l <= l1; l++) {
+        const V e = part[l * NP + (oo - (l * c) / len)];
+        t.x += e.x;
+        t.y += e.y;
+      }
+    }
+    done(oo, t);
+  }
+}
+
 // Steps 1 and 2: from the forward series arrays (Sa = a, Sc = c, SR, Sp, Sz, Se), the La Budde state
 // in W and the Hessenberg form in S, write H_bar into Kb (zeroed here).
 template <typename R, int G>
 __device__ __forceinline__ void adjoint_series_labudde(const typename Cx<R>::t* W, const typename Cx<R>::t* S,
                                                        typename Cx<R>::t* Kb, typename Cx<R>::t* Qb,
-                                                       typename Cx<R>::t* Cb, typename Cx<R>::t* Sb,
-                                                       const typename Cx<R>::t* Sa, const typename Cx<R>::t* Sc,
-                                                       const typename Cx<R>::t* SR, const typename Cx<R>::t* Sp,
-                                                       const typename Cx<R>::t* Sz, const typename Cx<R>::t* Se,
-                                                       int nd, int ld, int bord, int h, int H, int Hl, int lt) {
+                                                       typename Cx<R>::t* U, const typename Cx<R>::t* Sa,
+                                                       const typename Cx<R>::t* Sc, const typename Cx<R>::t* SR,
+                                                       const typename Cx<R>::t* Sp, const typename Cx<R>::t* Sz,
+                                                       const typename Cx<R>::t* Se, int nd, int ld, int bord, int h,
+                                                       int H, int Hl, int lt) {
   using V = typename Cx<R>::t;
   const V zero = cmake<V>((R)0, (R)0);
-  V* eb = Sb;
-  V* zb = Sb + (H + 2);
+  const int QW = Hl + 1;
+  V* eb = U;
+  V* zb = U + (H + 2);
   V* pb = zb + (H + 2);
   V* Rb = pb + (H + 2);
   V* ab = Rb + (H + 2);
   V* cb = ab + (H + 2);
-  for (int x = lt; x < 6 * (H + 2); x += G) Sb[x] = zero;
+  (void)Sc;
+  for (int x = lt; x < 6 * (H + 2); x += G) U[x] = zero;
   for (int x = lt; x < nd * ld; x += G) Kb[x] = zero;
-  for (int x = lt; x < (Hl + 1) * (Hl + 1); x += G) Qb[x] = zero;
+  for (int x = lt; x < (nd + 1) * QW; x += G) Qb[x] = zero;
   team_sync<G>();
   if (lt == 0) eb[h] = cmake<V>((R)1, (R)0);
   team_sync<G>();
@@ -120,87 +179,100 @@ __device__ __forceinline__ void adjoint_series_labudde(const typename Cx<R>::t* 
   for (int m = lt; m <= Hl; m += G) {
     const V a = (m <= H + 1) ? ab[m] : zero, c = (m <= H + 1) ? cb[m] : zero;
     if (bord) {
-      if (m <= nd - 1) Qb[1 * (Hl + 1) + m] = cmake<V>(a.x + c.x, a.y + c.y);
+      if (m <= nd - 1) Qb[QW + m] = cmake<V>(a.x + c.x, a.y + c.y);
       Qb[m] = cmake<V>(-c.x, -c.y);
     } else {
       Qb[m] = a;
     }
   }
   team_sync<G>();
-  // La Budde backwards: j = 0, 1, ..., nd - 1 (q_bar_j is complete when j is reached; step j
-  // writes rows j+1 .. j+Hl of the window, and row j's slot is cleared for row j + Hl + 1)
-  const int QW = Hl + 1;
+  // La Budde backwards, j = 0, 1, ..., nd - 1: q_bar_j is complete when j is reached (only earlier
+  // steps write row j). Step j pushes it into row j + 1 through the factor (1 - t h_jj) and into
+  // rows l + 1 through q_bar_(l+1)[m'] -= c_jl q_bar_j[m' + l - j + 1], l = j+1 .. j+D (D = degj - 1,
+  // m' = 0 .. D - 1 - x for l = j + 1 + x). The (x, m') items are flat: rows x and D - 1 - x share
+  // a block of D + 1 items.
   for (int j = 0; j < nd; j++) {
-    const int degj = min(Hl, nd - j);
-    const int nl = min(Hl - 1, nd - 1 - j);  // l = j+1 .. j+nl, d = l - j + 1 <= Hl
-    V* qbj = Qb + (j % QW) * QW;
-    for (int x = lt; x <= nl; x += G) {
-      if (x < nl) {
-        const int l = j + 1 + x, d = x + 2;
-        const V c = W[j * ld + l];  // c_jl (La Budde's table over H)
-        V* qbl = Qb + ((l + 1) % QW) * QW;
-        const int mmax = min(Hl - d, nd - l - 1);
-        V s = zero;
-        for (int mp = 0; mp <= mmax; mp++) {
-          const V g = qbj[mp + d];
-          cmac(s, g, q_fwd(W, ld, nd, l + 1, mp));
-          V t = qbl[mp];
-          cmsub(t, c, g);
-          qbl[mp] = t;
-        }
-        Cb[j * Hl + x] = cmake<V>(-s.x, -s.y);
-      } else {
-        const V hjj = S[j * ld + j];
-        V* qb1 = Qb + ((j + 1) % QW) * QW;
-        V s = zero;
-        for (int m = 0; m <= degj; m++) {
-          const V g = qbj[m];
-          V t = qb1[m];
-          if (m <= nd - j - 1) {
-            t.x += g.x;
-            t.y += g.y;
-          }
-          if (m + 1 <= degj) cmsub(t, hjj, qbj[m + 1]);
-          qb1[m] = t;
-          if (m >= 1) cmac(s, g, q_fwd(W, ld, nd, j + 1, m - 1));
-        }
-        Kb[j * ld + j] = cmake<V>(-s.x, -s.y);
+    const int degj = min(Hl, nd - j), D = degj - 1;
+    const V* qbj = Qb + j * QW;
+    V* qb1 = Qb + (j + 1) * QW;
+    const V hjj = S[j * ld + j];
+    for (int m = lt; m <= degj; m += G) {
+      V t = qb1[m];
+      const V g = qbj[m];
+      if (m <= nd - j - 1) {
+        t.x += g.x;
+        t.y += g.y;
       }
+      if (m + 1 <= degj) cmsub(t, hjj, qbj[m + 1]);
+      qb1[m] = t;
+    }
+    const int nitems = ((D + 1) >> 1) * (D + 1);
+    for (int w = lt; w < nitems; w += G) {
+      const int b = w / (D + 1), pos = w - b * (D + 1);
+      const bool first = pos < D - b;
+      const int x = first ? b : D - 1 - b;
+      if (!first && x == b) continue;  // odd D: the middle row belongs to its block once
+      const int mp = first ? pos : pos - (D - b);
+      const int l = j + 1 + x;
+      V* qbl = Qb + (l + 1) * QW;
+      V t = qbl[mp];
+      cmsub(t, W[j * ld + l], qbj[mp + x + 2]);
+      qbl[mp] = t;
     }
     team_sync<G>();
-    for (int m = lt; m < QW; m += G) qbj[m] = zero;  // row j is done: its slot serves row j + QW
-    team_sync<G>();
   }
-  // c_jl = h_jl P_j(l), P_j(l) = prod_(r=j+1..l) h_(r,r-1): h_bar_jl += c_bar_jl P_j(l) (lane per
-  // row j), and h_bar_(r,r-1) += sum over j < r <= l of c_bar_jl h_jl times the product without
-  // h_(r,r-1) (lane per r, so that no two lanes add into one entry)
+  // c_bar_jl = -sum_m' q_bar_j[m' + y + 2] q_(j+y+2)[m'] (y = l - j - 1 = 0 .. D - 1) and
+  // h_bar_jj = the same sum at y = -1, m' = 0 .. D - y - 1: one item per (y, j), y-major so that
+  // the items of a pass have nearly equal lengths
+  for (int w = lt; w < Hl * nd; w += G) {
+    const int yy = w / nd, j = w - yy * nd, y = yy - 1;
+    const int D = min(Hl, nd - j) - 1;
+    if (y >= D) continue;
+    const V* qb = Qb + j * QW + y + 2;
+    const int row = j + y + 2;
+    V s = zero;
+    for (int mp = 0; mp < D - y; mp++) cmac(s, qb[mp], q_fwd<V>(W, ld, nd, row, mp));
+    s.x = flip(s.x);
+    s.y = flip(s.y);
+    if (y < 0) {
+      Kb[j * ld + j] = s;
+    } else {
+      U[j * Hl + y] = s;
+    }
+  }
+  team_sync<G>();
+  // c_jl = h_jl P_j(l), P_j(l) = prod_(r=j+1..l) h_(r,r-1). Lane per row j: h_bar_jl += c_bar_jl P_j(l);
+  // then, backwards over l, T_j(l) = c_bar_jl h_jl + h_(l+1,l) T_j(l+1) and the share of row j in
+  // h_bar_(l,l-1), P_j(l-1) T_j(l), in place of c_bar_jl. Lane per r then adds the shares.
+  V* Pp = Qb;  // q_bar is spent
   for (int j = lt; j < nd; j += G) {
     const int nl = min(Hl - 1, nd - 1 - j);
     V P = cmake<V>((R)1, (R)0);
     for (int x = 0; x < nl; x++) {
       const int l = j + 1 + x;
+      Pp[j * Hl + x] = P;
       P = cmul(P, S[l * ld + l - 1]);
       V t = Kb[j * ld + l];
-      cmac(t, Cb[j * Hl + x], P);
+      cmac(t, U[j * Hl + x], P);
       Kb[j * ld + l] = t;
+    }
+    V T = zero;
+    for (int x = nl - 1; x >= 0; x--) {
+      const int l = j + 1 + x;
+      V t = cmul(U[j * Hl + x], S[j * ld + l]);
+      if (x < nl - 1) cmac(t, S[(l + 1) * ld + l], T);
+      T = t;
+      U[j * Hl + x] = cmul(Pp[j * Hl + x], T);
     }
   }
   team_sync<G>();
   for (int r = 1 + lt; r < nd; r += G) {
-    V acc = zero;
-    V pre = cmake<V>((R)1, (R)0);
-    for (int j = r - 1; j >= 0 && r - j <= Hl - 1; j--) {
-      if (j < r - 1) pre = cmul(pre, S[(j + 1) * ld + j]);
-      V suf = cmake<V>((R)1, (R)0);
-      const int lmax = min(j + Hl - 1, nd - 1);
-      for (int l = r; l <= lmax; l++) {
-        if (l > r) suf = cmul(suf, S[l * ld + l - 1]);
-        cmac(acc, cmul(Cb[j * Hl + (l - j - 1)], S[j * ld + l]), cmul(pre, suf));
-      }
-    }
     V t = Kb[r * ld + r - 1];
-    t.x += acc.x;
-    t.y += acc.y;
+    for (int j = max(0, r - Hl + 1); j < r; j++) {
+      const V e = U[j * Hl + r - j - 1];
+      t.x += e.x;
+      t.y += e.y;
+    }
     Kb[r * ld + r - 1] = t;
   }
   team_sync<G>();
@@ -208,86 +280,105 @@ __device__ __forceinline__ void adjoint_series_labudde(const typename Cx<R>::t* 
 
 // Step 3: the elimination backwards. S holds H with the multipliers of step k in column k below
 // the subdiagonal (entries below the subdiagonal are zero in the state itself), piv the pivot
-// rows. On return S is the input matrix K (up to rounding) and Kb its adjoint.
+// rows. On return S is the input matrix K (up to rounding) and Kb its adjoint. U holds the step's
+// multipliers l (U[0 .. nd)), their adjoints l_bar (U[nd .. 2 nd), with -sum l_bar l at index
+// k + 1) and the partial sums of team_dots.
 template <typename R, int G>
 __device__ __forceinline__ void adjoint_elimination(typename Cx<R>::t* S, typename Cx<R>::t* Kb,
-                                                    typename Cx<R>::t* Lv, typename Cx<R>::t* Lb, const int* piv,
-                                                    int nd, int ld, int lt) {
+                                                    typename Cx<R>::t* U, const int* piv, int nd, int ld, int lt) {
   using V = typename Cx<R>::t;
   constexpr int SG = G < 32 ? G : 32;
   const V zero = cmake<V>((R)0, (R)0);
+  V* Lv = U;
+  V* Lb = U + nd;
+  V* part = U + 2 * nd;
   for (int k = nd - 3; k >= 0; k--) {
-    const int k1 = k + 1, r = piv[k];
+    const int k1 = k + 1, r = piv[k], m = nd - k - 2;
     const V p = S[k1 * ld + k];
-    // multipliers of step k, and l_bar_a = (K'^T Kb'[:, k1])_a - (Kb' K'[k1, :]^T)_a for a >= k+2
-    // (row k1 of the state is zero left of column k)
-    V sl = zero;  // sum_a l_bar_a l_a (this lane's share)
-    for (int a = k + 2 + lt; a < nd; a += G) {
-      const V la = S[a * ld + k];
-      V s = zero;
-      for (int i = 0; i < nd; i++) cmac(s, S[i * ld + a], Kb[i * ld + k1]);
-      for (int j = k; j < nd; j++) cmsub(s, Kb[a * ld + j], S[k1 * ld + j]);
-      Lv[a] = la;
-      Lb[a] = s;
-      cmac(sl, s, la);
-    }
+    // l_bar_a = (K'^T Kb'[:, k1])_a - (Kb' K'[k1, :]^T)_a for a = k+2 .. nd-1 (row k1 of the state
+    // is zero left of column k): nd + nd - k products each
+    V sl = zero;  // sum_a l_bar_a l_a (this lane's outputs)
+    team_dots<R, G>(
+        m, 2 * nd - k, part, lt,
+        [&](int o, int q, V& x, V& y) {
+          const int a = k + 2 + o, j = k + q - nd;
+          const bool lo = q < nd;
+          x = lo ? S[q * ld + a] : Kb[a * ld + j];
+          y = lo ? Kb[q * ld + k1] : S[k1 * ld + j];
+          const V nx = cmake<V>(flip(x.x), flip(x.y));
+          x = lo ? x : nx;
+        },
+        [&](int o, V s) {
+          const int a = k + 2 + o;
+          const V la = S[a * ld + k];
+          Lv[a] = la;
+          Lb[a] = s;
+          cmac(sl, s, la);
+        });
 #pragma unroll
     for (int off = SG / 2; off >= 1; off >>= 1) {
       sl.x += __shfl_xor_sync(0xffffffffu, sl.x, off);
       sl.y += __shfl_xor_sync(0xffffffffu, sl.y, off);
     }
+    if (lt == 0) Lb[k1] = cmake<V>(flip(sl.x), flip(sl.y));
     team_sync<G>();
-    // A_bar = L^T Kb' (row k1 -= sum_a l_a Kb'[a][:]) and A = L^-1 K' (rows a >= k+2 += l_a K'[k1][:],
-    // column k set to l_a p), disjoint entries
-    for (int x = lt; x < 2 * nd; x += G) {
-      if (x < nd) {
-        const int j = x;
-        V t = Kb[k1 * ld + j];
-        for (int a = k + 2; a < nd; a++) cmsub(t, Lv[a], Kb[a * ld + j]);
-        Kb[k1 * ld + j] = t;
-      } else {
-        const int a = x - nd + k + 2;
-        if (a < nd) {
-          const V la = Lv[a];
-          S[a * ld + k] = cmul(la, p);
-          for (int j = k1; j < nd; j++) {
-            V t = S[a * ld + j];
-            cmac(t, la, S[k1 * ld + j]);
-            S[a * ld + j] = t;
-          }
-        }
-      }
+    // A = L^-1 K' on rows a >= k+2: A[a][k] = l_a p, A[a][j] = K'[a][j] + l_a K'[k1][j] (j >= k1);
+    // item (a, column), column k first
+    for (int w = lt; w < m * (m + 2); w += G) {
+      const int o = w / (m + 2), cc = w - o * (m + 2);
+      const int a = k + 2 + o, j = k + cc;
+      V t = S[a * ld + j];
+      const V y = cc == 0 ? p : S[k1 * ld + j];
+      t = cc == 0 ? zero : t;
+      cmac(t, Lv[a], y);
+      S[a * ld + j] = t;
     }
+    // A_bar = L^T Kb' on row k1: Kb[k1][j] -= sum_a l_a Kb'[a][j]
+    team_dots<R, G>(
+        nd, m, part, lt,
+        [&](int o, int q, V& x, V& y) {
+          const int a = k + 2 + q;
+          x = Lv[a];
+          y = Kb[a * ld + o];
+        },
+        [&](int o, V s) {
+          V t = Kb[k1 * ld + o];
+          t.x -= s.x;
+          t.y -= s.y;
+          Kb[k1 * ld + o] = t;
+        });
     team_sync<G>();
-    // A_bar = (L^T Kb') L^-T (columns a >= k+2 += A_bar[:, k1] l_a), the multiplier adjoints
-    // (A_bar[a][k] += l_bar_a / p, A_bar[k1][k] -= sum l_bar l / p), and A = (L^-1 K') L
-    // (column k1 -= sum_a A[:, a] l_a)
+    // A_bar = (L^T Kb') L^-T on columns a >= k+2 (Kb[i][a] += Kb[i][k1] l_a), then the multiplier
+    // adjoints Kb[a][k] += l_bar_a / p (a >= k+2) and Kb[k1][k] -= (sum_a l_bar_a l_a) / p: one
+    // flat list of multiply-adds
     const V ip = crecip(p);
-    for (int x = lt; x < 2 * nd; x += G) {
-      if (x < nd) {
-        const int i = x;
-        const V ck = Kb[i * ld + k1];
-        for (int a = k + 2; a < nd; a++) {
-          V t = Kb[i * ld + a];
-          cmac(t, ck, Lv[a]);
-          Kb[i * ld + a] = t;
-        }
-        if (i >= k + 2) {
-          V t = Kb[i * ld + k];
-          cmac(t, Lb[i], ip);
-          Kb[i * ld + k] = t;
-        } else if (i == k1) {
-          V t = Kb[i * ld + k];
-          cmsub(t, sl, ip);
-          Kb[i * ld + k] = t;
-        }
-      } else {
-        const int i = x - nd;
-        V t = S[i * ld + k1];
-        for (int a = k + 2; a < nd; a++) cmsub(t, S[i * ld + a], Lv[a]);
-        S[i * ld + k1] = t;
-      }
+    const int n3 = nd * m;
+    for (int w = lt; w < n3 + m + 1; w += G) {
+      const bool cl = w < n3;
+      const int i = cl ? w / m : 0;
+      const int a = cl ? k + 2 + (w - i * m) : k1 + (w - n3);
+      V* pt = cl ? Kb + i * ld + a : Kb + a * ld + k;
+      const V x = cl ? Kb[i * ld + k1] : Lb[a];
+      const V la = Lv[a];
+      const V y = cl ? la : ip;
+      V t = *pt;
+      cmac(t, x, y);
+      *pt = t;
     }
+    // A = (L^-1 K') L on column k1: A[i][k1] -= sum_a A[i][a] l_a
+    team_dots<R, G>(
+        nd, m, part, lt,
+        [&](int o, int q, V& x, V& y) {
+          const int a = k + 2 + q;
+          x = S[o * ld + a];
+          y = Lv[a];
+        },
+        [&](int o, V s) {
+          V t = S[o * ld + k1];
+          t.x -= s.x;
+          t.y -= s.y;
+          S[o * ld + k1] = t;
+        });
     team_sync<G>();
     // swap indices r and k1 back: rows (state: columns >= k; adjoint: every column), then columns.
     // Run by every team whatever its r (a swap of k1 with itself changes nothing): the teams of a

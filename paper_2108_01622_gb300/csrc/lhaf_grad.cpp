@@ -62,8 +62,8 @@ lhaf_status grad_plan(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128*
   if (pl.N == 0) return LHAF_OK;
   const int nd = pl.nd, n = nd - pl.bord;
   // team size: largest number of resident warps, preferring 16 or 32 lanes per term
-  const size_t tb = grad_team_bytes(nd, pl.H, pl.h, pl.bord);
   const size_t ib = cta_table_bytes(false, pl.Hl, pl.H);
+  size_t tb = 0;
   int occ = 0;
   double best = -1.0;
   J.team = 0;
@@ -71,7 +71,8 @@ lhaf_status grad_plan(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128*
   const int forced = env ? std::atoi(env) : 0;
   for (int g : {16, 32, 8}) {  // teams inside one warp (the adjoint's reductions are warp shuffles)
     if (forced && g != forced) continue;
-    const size_t smem = ib + (size_t)teams_per_cta(g) * tb;
+    const size_t tg = grad_team_bytes(nd, pl.H, pl.h, pl.bord, g);
+    const size_t smem = ib + (size_t)teams_per_cta(g) * tg;
     if (smem > 227 * 1024) continue;
     const int o = grad_ctas_per_sm(g, smem);
     if (o <= 0) continue;
@@ -81,6 +82,7 @@ lhaf_status grad_plan(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128*
       best = score;
       J.team = g;
       occ = o;
+      tb = tg;
     }
   }
   if (J.team == 0) return LHAF_ETOOBIG;

@@ -152,7 +152,7 @@ cudaError_t launch_batch_gather(const double2* B, long long B_stride, const doub
                                 double2* chat_pool, float2* chat32_pool, cudaStream_t stream);
 
 // Adjoint: shared bytes per team, occupancy, the value+gradient kernel and the cross-team sum.
-size_t grad_team_bytes(int nd, int H, int h, int bord);
+size_t grad_team_bytes(int nd, int H, int h, int bord, int team);  // team: 8, 16 or 32 lanes
 int grad_ctas_per_sm(int team, size_t smem_bytes);
 cudaError_t launch_grad(int team, const double2* chat, const TermParams& p, int grid, double* partials,
                         double2* gpart, cudaStream_t stream);

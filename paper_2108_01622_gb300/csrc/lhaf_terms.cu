@@ -289,11 +289,8 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
   V* gS = reinterpret_cast<V*>(reinterpret_cast<unsigned char*>(ts) + ((sizeof(TeamScratch) + 15) & ~(size_t)15));
   V* gK = gS + nd * ld;
   V* gQ = gK + nd * ld;
-  V* gC = gQ + (Hl + 1) * (Hl + 1);
-  V* gSb = gC + nd * Hl;
-  V* gLv = gSb + 6 * (H + 2);
-  V* gLb = gLv + nd;
-  int* gpiv = reinterpret_cast<int*>(gLb + nd);
+  V* gU = gQ + (nd + 1) * (Hl + 1);
+  int* gpiv = reinterpret_cast<int*>(gU + adjoint_union(nd, H, Hl, G));
   V* gA = GRAD ? gpart + (size_t)team_global * (size_t)(ng * ng + ng) : nullptr;
   V* gV = GRAD ? gA + ng * ng : nullptr;
   if constexpr (GRAD) {
@@ -952,8 +949,8 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
       }
       team_sync<G>();
       if constexpr (GRAD) {
-        adjoint_series_labudde<R, G>(W, gS, gK, gQ, gC, gSb, Sa, Sc, SR, Sp, Sz, Se, nd, ld, bord, h, H, Hl, lt);
-        adjoint_elimination<R, G>(gS, gK, gLv, gLb, gpiv, nd, ld, lt);
+        adjoint_series_labudde<R, G>(W, gS, gK, gQ, gU, Sa, Sc, SR, Sp, Sz, Se, nd, ld, bord, h, H, Hl, lt);
+        adjoint_elimination<R, G>(gS, gK, gU, gpiv, nd, ld, lt);
         adjoint_accumulate<R, G>(gK, nd, ld, bord, ts->delta, ts->weight, gA, gV, lt);
       }
     }
@@ -1837,15 +1834,16 @@ cudaError_t launch_item_finalize(const double* acc, const int* item_h, int n_ite
 
 size_t cta_table_bytes(bool fp32, int Hl, int H) { return items_bytes_of(fp32, Hl, H); }
 
-size_t grad_team_bytes(int nd, int H, int h, int bord) {
+size_t grad_team_bytes(int nd, int H, int h, int bord, int team) {
   (void)h;
-  const int n = nd - bord, ld = nd | 1, Hl = H < nd ? H : nd;
+  (void)bord;
+  const int ld = nd | 1, Hl = H < nd ? H : nd;
   // team_shared_bytes covers the working matrix, the series arrays and the team scratch (ending
-  // 16-byte aligned, where the adjoint's buffers start)
+  // 16-byte aligned, where the adjoint's buffers start): then S, Kb, q_bar and the phase-shared
+  // region of the adjoint, and the pivot rows
   size_t b = team_shared_bytes(false, nd, H, 0, false);
-  (void)n;
-  b += (2 * (size_t)nd * ld + (size_t)(Hl + 1) * (Hl + 1) + (size_t)nd * Hl + 6 * (size_t)(H + 2) + 2 * (size_t)nd) *
-       sizeof(double2);
+  const int G = team == 8 || team == 16 ? team : 32;
+  b += (2 * (size_t)nd * ld + (size_t)(nd + 1) * (Hl + 1) + (size_t)adjoint_union(nd, H, Hl, G)) * sizeof(double2);
   b += (size_t)nd * sizeof(int);
   return (b + 15) & ~(size_t)15;
 }
