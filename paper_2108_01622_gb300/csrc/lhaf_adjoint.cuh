@@ -1,5 +1,5 @@
 // Adjoint of one sieve term by reverse mode through the forward steps themselves (included by
-// lhaf_terms.cu after its complex helpers; teams of at most one warp).
+// lhaf_terms.cu after its complex helpers; teams of 8, 16, 32 or 64 lanes).
 //
 // The forward term (lhaf_terms.cu, sieve_terms) reduces the bordered matrix K = [[0, u], [v^T, M]]
 // (M = C X_delta', u = v X_delta') to Hessenberg form H by stabilised elementary similarities
@@ -319,6 +319,16 @@ __device__ __forceinline__ void adjoint_elimination(typename Cx<R>::t* S, typena
     for (int off = SG / 2; off >= 1; off >>= 1) {
       sl.x += __shfl_xor_sync(0xffffffffu, sl.x, off);
       sl.y += __shfl_xor_sync(0xffffffffu, sl.y, off);
+    }
+    if constexpr (G > 32) {  // two warps: their sums meet in the (now free) partials
+      team_sync<G>();
+      if ((lt & 31) == 0) part[lt >> 5] = sl;
+      team_sync<G>();
+      sl = part[0];
+      for (int w = 1; w < G / 32; w++) {
+        sl.x += part[w].x;
+        sl.y += part[w].y;
+      }
     }
     if (lt == 0) Lb[k1] = cmake<V>(flip(sl.x), flip(sl.y));
     team_sync<G>();

@@ -67,9 +67,9 @@ lhaf_status grad_plan(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128*
   int occ = 0;
   double best = -1.0;
   J.team = 0;
-  const char* env = std::getenv("LHAF_GRAD_TEAM");  // forces 8, 16 or 32 lanes per term
+  const char* env = std::getenv("LHAF_GRAD_TEAM");  // forces 8, 16, 32 or 64 lanes per term
   const int forced = env ? std::atoi(env) : 0;
-  for (int g : {16, 32, 8}) {  // teams inside one warp (the adjoint's reductions are warp shuffles)
+  for (int g : {16, 32, 8, 64}) {
     if (forced && g != forced) continue;
     const size_t tg = grad_team_bytes(nd, pl.H, pl.h, pl.bord, g);
     const size_t smem = ib + (size_t)teams_per_cta(g) * tg;

@@ -280,11 +280,11 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
   const V one = cmake<V>((R)1, (R)0);
   double acc_re = 0.0, acc_re_lo = 0.0, acc_im = 0.0, acc_im_lo = 0.0;
 
-  // adjoint buffers (GRAD, teams of at most one warp): S and Kb (nd x ld each), q_bar
-  // ((Hl + 1) x (Hl + 1) window), c_bar (nd x Hl), series adjoints (6 x (H + 2)), multipliers and their
-  // adjoints (nd each), pivot rows (nd ints) in shared memory; the gradient sums Ga (n x n) and
-  // Gv (n) in the team's own slice of gpart (global memory: the freed shared memory lets a fourth
-  // team onto an SM at n = 27, measured 34.1 -> 25.9 ms for a 32-photon outcome)
+  // adjoint buffers (GRAD): S and Kb (nd x ld each), q_bar ((nd + 1) x (Hl + 1)), the region that
+  // the adjoint's phases share (series adjoints, then c_bar, then multipliers, their adjoints and
+  // dot-product partials: adjoint_union entries) and the pivot rows (nd ints) in shared memory; the
+  // gradient sums Ga (n x n) and Gv (n) in the team's own slice of gpart (global memory, which
+  // leaves shared memory for a fourth CTA on an SM at n = 27)
   const int ng = nd - bord;
   V* gS = reinterpret_cast<V*>(reinterpret_cast<unsigned char*>(ts) + ((sizeof(TeamScratch) + 15) & ~(size_t)15));
   V* gK = gS + nd * ld;
@@ -1842,7 +1842,7 @@ size_t grad_team_bytes(int nd, int H, int h, int bord, int team) {
   // 16-byte aligned, where the adjoint's buffers start): then S, Kb, q_bar and the phase-shared
   // region of the adjoint, and the pivot rows
   size_t b = team_shared_bytes(false, nd, H, 0, false);
-  const int G = team == 8 || team == 16 ? team : 32;
+  const int G = team == 8 || team == 16 || team == 64 ? team : 32;
   b += (2 * (size_t)nd * ld + (size_t)(nd + 1) * (Hl + 1) + (size_t)adjoint_union(nd, H, Hl, G)) * sizeof(double2);
   b += (size_t)nd * sizeof(int);
   return (b + 15) & ~(size_t)15;
@@ -1850,12 +1850,13 @@ size_t grad_team_bytes(int nd, int H, int h, int bord, int team) {
 
 template <int G> static const void* gptr() { return (const void*)grad_kernel<G>; }
 
-// The adjoint's reductions run inside one warp: teams of 8, 16 or 32 lanes.
+// Teams of 8, 16 or 32 lanes inside one warp, or of two warps (64 lanes).
 static const void* pick_grad(int team) {
   switch (team) {
     case 8: return gptr<8>();
     case 16: return gptr<16>();
     case 32: return gptr<32>();
+    case 64: return gptr<64>();
   }
   return nullptr;
 }

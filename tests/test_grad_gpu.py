@@ -4,6 +4,7 @@ through the GBS log-probability (torch.autograd)."""
 import numpy as np
 import pytest
 
+from oracle import csieve
 from oracle import lhaf_oracle as lo
 from paper_2108_01622_gb300 import workloads as wl
 from tests.libutil import ensure_built
@@ -89,6 +90,44 @@ def test_grad_32_photon_outcome_against_oracle_minors(ctx):
         r = reps.copy()
         r[m] -= 1
         ref = reps[m] * lo.lhaf_repeated(B, g, r)
+        assert abs(dg[m] - ref) <= 1e-9 * abs(ref)
+
+
+@pytest.mark.parametrize("team", [8, 16, 32, 64])
+def test_grad_every_team_size(ctx, team, monkeypatch):
+    # the adjoint's team forced to 8, 16, 32 and 64 lanes: the same minors as the default choice
+    monkeypatch.setenv("LHAF_GRAD_TEAM", str(team))
+    for reps, loops in (((3, 2, 2, 1), True), ((2, 1, 2, 2, 1), False)):
+        p = wl.small_problem(seed=5 + len(reps), M=len(reps), reps=reps, loops=loops)
+        val, dB, dg = ctx.lhaf_grad(p.B, p.gamma, p.reps)
+        dB_ref, dg_ref = lo.lhaf_grad_minor(p.B, p.gamma, p.reps)
+        scale = max(np.abs(dB_ref).max(), np.abs(dg_ref).max(), abs(val))
+        assert np.abs(dB - dB_ref).max() <= 1e-10 * scale
+        assert np.abs(dg - dg_ref).max() <= 1e-10 * scale
+
+
+def test_grad_37_wide_against_c_oracle_minors(ctx):
+    # 36 photons on distinct modes of a 40-mode state: working dimension 37 (more rows than the
+    # 32 lanes of a team); sampled entries against minors from the C oracle's sieve
+    b = wl.gradient_batch(seed=11, count=1, n_photons=2)
+    rng = np.random.default_rng(11)
+    reps = np.zeros(40, np.int32)
+    reps[rng.choice(40, 36, replace=False)] = 1
+    B, g = b.B, b.gammas[0]
+    val, dB, dg = ctx.lhaf_grad(B, g, reps)
+    ref_val = csieve.lhaf(B, g, reps)
+    assert abs(val - ref_val) <= 1e-10 * abs(ref_val)
+    occ = np.nonzero(reps)[0]
+    for m, mp in [(occ[0], occ[1]), (occ[7], occ[30]), (occ[35], occ[2])]:
+        r = reps.copy()
+        r[m] -= 1
+        r[mp] -= 1
+        ref = csieve.lhaf(B, g, r)
+        assert abs(dB[m, mp] - ref) <= 1e-9 * abs(ref), (m, mp)
+    for m in (occ[3], occ[34]):
+        r = reps.copy()
+        r[m] -= 1
+        ref = csieve.lhaf(B, g, r)
         assert abs(dg[m] - ref) <= 1e-9 * abs(ref)
 
 
