@@ -485,10 +485,28 @@ def run_extras(ctx, torch, dev, lg, workload):
             plan.run(Bd, Gd, out=og)
             tg_ = _timed(torch, lambda: plan.run(Bd, Gd, out=og), reps=1)
         d = torch.maximum((ob - op).abs() / op.abs(), (og - op).abs() / op.abs())
+        # the most cancelling items against the C oracle's long double values (tests/golden): an FP64
+        # sum keeps about 16 - log10(condition) digits, whichever form evaluates it
+        ill = []
+        gpath = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
+                             "chain_rule_ill_conditioned.json")
+        if os.path.exists(gpath):
+            with open(gpath) as f:
+                for it in json.load(f)["items"]:
+                    i, ref = it["index"], complex(*it["value"])
+                    e = {k: abs(complex(v[i].item()) - ref) / abs(ref) for k, v in (("batched", ob), ("plain", op),
+                                                                                    ("graph", og))}
+                    ill.append({"index": i, "photons": it["photons"], "condition": it["condition"],
+                                "bound_cond_x_2^-52": it["condition"] * 2.0 ** -52,
+                                "rel_err_batched": e["batched"], "rel_err_plain": e["plain"],
+                                "rel_err_graph": e["graph"],
+                                "rel_err_fp64_c_oracle": abs(complex(*it["fp64_c_oracle"]) - ref) / abs(ref)})
         out["batched"] = {"workload": "chain-rule batch: 4096 loop hafnians, 50-mode lossy GBS state, N~U{10..40}",
                           "batched_ms": tb, "graph_replay_ms": tg_, "plain_ms": tp,
                           "batched_over_plain_speedup": tp / tb, "graph_over_plain_speedup": tp / tg_,
-                          "max_rel_diff": float(d.max().item())}
+                          "max_rel_diff": float(d.max().item()),
+                          "items_rel_diff_over_1e-10": int((d > 1e-10).sum().item()),
+                          "ill_conditioned_items_vs_extended_oracle": ill}
 
     def _batched_small():
         # small items only: many short loop hafnians, where one launch per item is launch-bound

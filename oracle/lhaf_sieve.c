@@ -1,7 +1,9 @@
 /* Test infrastructure only: a plain C restatement of the repeated-pair finite difference sieve
  * (App. B.2 and B.4, Eq. fdsieve, per-term function of Eq. ET_poly), used as the timed CPU
  * baseline and checked against the numpy oracle, brute force and closed forms. It shares nothing
- * with the GPU library. Complex FP64 (C99 double complex); sums in long double.
+ * with the GPU library. Complex FP64 (C99 double complex); sums in long double. Built with
+ * LHAF_ORACLE_EXTENDED defined, the same steps run in long double complex (a 64-bit significand on
+ * x86-64): an extended-precision reference of the same sum for ill-conditioned loop hafnians.
  *
  * One term, digit vector k (k_i in 0..eta_i), delta'_i = eta_i - 2 k_i, weight
  * prod_i C(eta_i, k_i) (-1)^k_i. With the reduced slot matrix C (n = 2H slots; slot i < H is the
@@ -13,8 +15,7 @@
  *   g_k = p_k / (2k) + s_k / 2,   f = [t^h] exp(sum_k g_k t^k),
  * and lhaf = 2^-h sum_k weight(k) f(k) over every digit vector (no halving).
  * Terms are numbered as itertools.product over the digit ranges (first digit slowest). */
-#include <complex.h>
-#include <math.h>
+#include <tgmath.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -22,7 +23,13 @@
 #include <omp.h>
 #endif
 
+#ifdef LHAF_ORACLE_EXTENDED
+typedef long double real_t;
+typedef long double complex cplx;
+#else
+typedef double real_t;
 typedef double complex cplx;
+#endif
 
 #define MAXN 64
 
@@ -31,21 +38,21 @@ typedef double complex cplx;
 static void hessenberg_householder(int n, cplx* A) {
   cplx w[MAXN];
   for (int k = 0; k + 2 < n; k++) {
-    double norm2 = 0.0;
+    real_t norm2 = 0.0;
     for (int i = k + 1; i < n; i++) norm2 += creal(A[i * n + k]) * creal(A[i * n + k]) +
                                              cimag(A[i * n + k]) * cimag(A[i * n + k]);
     if (norm2 == 0.0) continue;
-    const double alpha = sqrt(norm2);
+    const real_t alpha = sqrt(norm2);
     const cplx x0 = A[(k + 1) * n + k];
-    const double ax0 = cabs(x0);
+    const real_t ax0 = cabs(x0);
     const cplx phase = ax0 > 0.0 ? x0 / ax0 : 1.0;
     for (int i = 0; i < n; i++) w[i] = 0.0;
     for (int i = k + 1; i < n; i++) w[i] = A[i * n + k];
     w[k + 1] += phase * alpha; /* w = x + e^{i arg x0} |x| e_1 */
-    double ww = 0.0;
+    real_t ww = 0.0;
     for (int i = k + 1; i < n; i++) ww += creal(w[i]) * creal(w[i]) + cimag(w[i]) * cimag(w[i]);
     if (ww == 0.0) continue;
-    const double beta = 2.0 / ww;
+    const real_t beta = 2.0 / ww;
     /* A <- H A: rows k+1.. */
     for (int j = 0; j < n; j++) {
       cplx d = 0.0;
@@ -93,15 +100,15 @@ static cplx exp_coefficient(int h, const cplx* g) {
   e[0] = 1.0;
   for (int m = 1; m <= h; m++) {
     cplx s = 0.0;
-    for (int k = 1; k <= m; k++) s += (double)k * g[k] * e[m - k];
-    e[m] = s / (double)m;
+    for (int k = 1; k <= m; k++) s += (real_t)k * g[k] * e[m - k];
+    e[m] = s / (real_t)m;
   }
   return e[h];
 }
 
-static double binom(int n, int k) {
-  double c = 1.0;
-  for (int i = 1; i <= k; i++) c = c * (double)(n - k + i) / (double)i;
+static real_t binom(int n, int k) {
+  real_t c = 1.0;
+  for (int i = 1; i <= k; i++) c = c * (real_t)(n - k + i) / (real_t)i;
   return c;
 }
 
@@ -113,9 +120,9 @@ static cplx term_f(int n, int H, const cplx* C, const cplx* v, const int* delta,
   for (int a = 0; a < n; a++)
     for (int j = 0; j < n; j++) {
       const int pj = j < H ? j + H : j - H, dj = delta[j < H ? j : j - H];
-      M[a * n + j] = C[a * n + pj] * (double)dj;
+      M[a * n + j] = C[a * n + pj] * (real_t)dj;
     }
-  for (int j = 0; j < n; j++) u[j] = v[j < H ? j + H : j - H] * (double)delta[j < H ? j : j - H];
+  for (int j = 0; j < n; j++) u[j] = v[j < H ? j + H : j - H] * (real_t)delta[j < H ? j : j - H];
   /* loop terms s_k = u M^(k-1) v^T, k = 1..h */
   cplx s[MAXN + 1];
   for (int i = 0; i < n; i++) x[i] = v[i];
@@ -142,7 +149,7 @@ static cplx term_f(int n, int H, const cplx* C, const cplx* v, const int* delta,
       cplx acc = 0.0;
       const int jm = k - 1 < n ? k - 1 : n;
       for (int j = 1; j <= jm; j++) acc += c[j] * p[k - j];
-      p[k] = -acc - (k <= n ? (double)k * c[k] : 0.0);
+      p[k] = -acc - (k <= n ? (real_t)k * c[k] : 0.0);
     }
   } else {
     cplx P[MAXN * MAXN], Q[MAXN * MAXN];
@@ -168,7 +175,8 @@ static cplx term_f(int n, int H, const cplx* C, const cplx* v, const int* delta,
 
 /* Sum of weight * f over the digit vectors numbered [start, stop) (itertools.product order over
  * k_i in 0..eta_i, first digit slowest), unscaled. C: n x n complex as interleaved (re, im)
- * doubles, v: n complex, eta: H repeat counts (n = 2H). out: (re_hi, re_lo, im_hi, im_lo).
+ * doubles, v: n complex, eta: H repeat counts (n = 2H). out: (re_hi, re_lo, im_hi, im_lo, sum of
+ * |weight * f|), the last for the sum's condition number.
  * threads <= 0: OpenMP's default. Returns the number of threads used, or -1 on bad sizes. */
 int oracle_sieve_sum(int H, const double* C_ri, const double* v_ri, const int* eta, int h, uint64_t start,
                      uint64_t stop, int hess, int threads, double* out) {
@@ -183,12 +191,12 @@ int oracle_sieve_sum(int H, const double* C_ri, const double* v_ri, const int* e
   }
   for (int i = 0; i < n * n; i++) C[i] = C_ri[2 * i] + I * C_ri[2 * i + 1];
   for (int i = 0; i < n; i++) v[i] = v_ri[2 * i] + I * v_ri[2 * i + 1];
-  long double sr = 0.0L, si = 0.0L;
+  long double sr = 0.0L, si = 0.0L, sa = 0.0L;
   int used = 1;
 #ifdef _OPENMP
   if (threads > 0) omp_set_num_threads(threads);
 #endif
-#pragma omp parallel reduction(+ : sr, si)
+#pragma omp parallel reduction(+ : sr, si, sa)
   {
 #ifdef _OPENMP
 #pragma omp single
@@ -197,7 +205,7 @@ int oracle_sieve_sum(int H, const double* C_ri, const double* v_ri, const int* e
 #pragma omp for schedule(dynamic, 16)
     for (long long t = (long long)start; t < (long long)stop; t++) {
       int delta[MAXN];
-      double w = 1.0;
+      real_t w = 1.0;
       unsigned long long r = (unsigned long long)t;
       for (int i = H - 1; i >= 0; i--) {
         const int k = (int)(r % (unsigned long long)(eta[i] + 1));
@@ -208,12 +216,14 @@ int oracle_sieve_sum(int H, const double* C_ri, const double* v_ri, const int* e
       const cplx f = (n == 0) ? 1.0 : term_f(n, H, C, v, delta, h, hess);
       sr += (long double)(w * creal(f));
       si += (long double)(w * cimag(f));
+      sa += (long double)(fabs(w) * cabs(f));
     }
   }
   out[0] = (double)sr;
   out[1] = (double)(sr - (long double)out[0]);
   out[2] = (double)si;
   out[3] = (double)(si - (long double)out[2]);
+  out[4] = (double)sa;
   free(C);
   free(v);
   return used;

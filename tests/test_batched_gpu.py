@@ -95,3 +95,28 @@ def test_batched_per_item_B_and_device_pointers(ctx, lg):
                                    flags=lg.BATCH_B_PER_ITEM)
     torch.cuda.synchronize()
     assert np.all(np.abs(out.cpu().numpy() - host) <= 1e-13 * np.abs(host))
+
+
+def test_ill_conditioned_chain_rule_items_against_extended_oracle(ctx, lg):
+    # The most cancelling items of the 4096-item chain-rule batch (sum |weight f| / |sum| = 8e6 ..
+    # 5e7) against the C oracle's long double values (tests/golden, written by the committed
+    # script beside them): an FP64 sum of such terms keeps about 16 - log10(condition) digits, so
+    # the bound is condition x 2^-52 (the FP64 C oracle itself is 1.8e-10 off on the worst item),
+    # for the batched form and for one call per item alike.
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "chain_rule_ill_conditioned.json")) as f:
+        gold = json.load(f)["items"]
+    b = wl.chain_rule_batch(seed=3, count=4096)
+    idx = [it["index"] for it in gold]
+    R = np.array([b.reps[i] for i in idx], dtype=np.int32)
+    G = np.array([b.gammas[i] for i in idx])
+    vals, st = ctx.lhaf_batched(b.B, G, R)
+    assert np.all(st == 0)
+    for k, it in enumerate(gold):
+        ref = complex(*it["value"])
+        tol = max(TOL, it["condition"] * 2.0 ** -52)
+        assert rel(vals[k], ref) <= tol, (it["index"], rel(vals[k], ref), tol)
+        assert rel(ctx.lhaf(b.B, G[k], R[k]), ref) <= tol
+        assert rel(complex(*it["fp64_c_oracle"]), ref) <= tol  # the FP64 oracle meets the same bound
