@@ -243,7 +243,12 @@ lhaf_status lhaf_multi_gamma(lhaf_ctx* ctx, int M, const lhaf_c128* B, int n_gam
  *           and B_m'm one variable; the library reads i <= j only).
  *   dgamma: HOST M or NULL; d lhaf / d gamma_m. With gamma == NULL the loops are diag(B): their
  *           derivative is added to dB[m][m] and dgamma is not written.
- * Host pointers only (LHAF_DEVICE_PTRS and LHAF_FP32_TERMS give LHAF_EINVAL). */
+ * The adjoint runs in reverse through the term's own steps (series, La Budde's recurrence, the
+ * elimination). As in lhaf, the middle digits of even-eta pairs run as zero-digit groups on their
+ * smaller matrices (at most 4096 groups; LHAF_NO_ZERO_SPLIT: every term on the full matrix).
+ * flags: LHAF_PLAIN_ACCUM, LHAF_NO_ZERO_SPLIT, LHAF_NO_REPEAT_SPEEDUP. The environment variable
+ * LHAF_GRAD_TEAM = 8, 16, 32 or 64 forces the lanes per term (default: the most resident warps).
+ * Host pointers only (LHAF_DEVICE_PTRS, LHAF_FP32_TERMS and LHAF_ET give LHAF_EINVAL). */
 lhaf_status lhaf_grad(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128* gamma, const int32_t* reps,
                       uint32_t flags, lhaf_c128* value, lhaf_c128* dB, lhaf_c128* dgamma);
 

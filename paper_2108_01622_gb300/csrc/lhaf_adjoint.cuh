@@ -417,11 +417,13 @@ __device__ __forceinline__ void adjoint_elimination(typename Cx<R>::t* S, typena
 }
 
 // Step 4: Ga[a][b] += weight * dC[a][b], Gv[b] += weight * dv[b] from K_bar, with K[i][bord + s] =
-// chat[i][bord + (s ^ 1)] * delta'(s) for slot s and the border column unscaled.
+// chat[i][bord + (s ^ 1)] * delta'(s) for slot s and the border column unscaled. With a slot map
+// (a zero-digit group's sieve), slot s of this sieve is slot smap[s] of the full problem, whose
+// n_full x n_full (then n_full) sums Ga (Gv) hold.
 template <typename R, int G>
 __device__ __forceinline__ void adjoint_accumulate(const typename Cx<R>::t* Kb, int nd, int ld, int bord,
                                                    const int* delta, double weight, typename Cx<R>::t* Ga,
-                                                   typename Cx<R>::t* Gv, int lt) {
+                                                   typename Cx<R>::t* Gv, const int* smap, int n_full, int lt) {
   using V = typename Cx<R>::t;
   const int n = nd - bord;
   const R wr = (R)weight;
@@ -429,19 +431,21 @@ __device__ __forceinline__ void adjoint_accumulate(const typename Cx<R>::t* Kb, 
     const int a = w / n, b = w - (w / n) * n;
     const R s = wr * (R)delta[b >> 1];
     const V g = Kb[(bord + a) * ld + bord + (b ^ 1)];
-    V t = Ga[w];
+    const int o = smap ? smap[a] * n_full + smap[b] : w;
+    V t = Ga[o];
     t.x = rfma(g.x, s, t.x);
     t.y = rfma(g.y, s, t.y);
-    Ga[w] = t;
+    Ga[o] = t;
   }
   if (bord) {
     for (int b = lt; b < n; b += G) {
       const V g0 = Kb[bord + (b ^ 1)], g1 = Kb[(bord + b) * ld];
       const R dl = (R)delta[b >> 1];
-      V t = Gv[b];
+      const int o = smap ? smap[b] : b;
+      V t = Gv[o];
       t.x = rfma(wr, rfma(g0.x, dl, g1.x), t.x);
       t.y = rfma(wr, rfma(g0.y, dl, g1.y), t.y);
-      Gv[b] = t;
+      Gv[o] = t;
     }
   }
   team_sync<G>();

@@ -26,7 +26,17 @@ struct GradJob {
   uint64_t grid = 0;
   int len = 0;  // n * n slot-matrix entries, then n loop entries
   TermParams p;
+  // zero-digit groups (empty: one sieve on the full matrix): their plans, descriptors (slot
+  // matrices at chat_off in a pool of `pool` entries) and chunk offsets
+  std::vector<Plan> subs;
+  std::vector<GradSieve> sv;
+  std::vector<long long> chunk_off;
+  size_t pool = 0;
 };
+
+// At most this many zero-digit groups per loop hafnian run as one grouped adjoint launch (more,
+// and the full matrix is used: the descriptors would outweigh the saved work).
+constexpr size_t kGradMaxSieves = 4096;
 
 lhaf_status grad_validate(int M, const lhaf_c128* B, const lhaf_c128* gamma, const int32_t* reps) {
   for (int i = 0; i < M; i++) {
@@ -61,7 +71,13 @@ lhaf_status grad_plan(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128*
   }
   if (pl.N == 0) return LHAF_OK;
   const int nd = pl.nd, n = nd - pl.bord;
-  // team size: largest number of resident warps, preferring 16 or 32 lanes per term
+  // zero-digit groups (App. B.4's middle digits of even pairs give delta' = 0, deleting two slots):
+  // the adjoint runs every group on its own smaller matrix unless LHAF_NO_ZERO_SPLIT is given
+  std::vector<Plan> subs;
+  const bool grouped = !(flags & LHAF_NO_ZERO_SPLIT) && split_zero_digits(pl, subs) && subs.size() >= 2 &&
+                       subs.size() <= kGradMaxSieves;
+  // team size: largest number of resident warps, preferring 16 or 32 lanes per term (the full plan
+  // has the largest matrix and tables of all its groups)
   const size_t ib = cta_table_bytes(false, pl.Hl, pl.H);
   size_t tb = 0;
   int occ = 0;
@@ -74,7 +90,7 @@ lhaf_status grad_plan(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128*
     const size_t tg = grad_team_bytes(nd, pl.H, pl.h, pl.bord, g);
     const size_t smem = ib + (size_t)teams_per_cta(g) * tg;
     if (smem > 227 * 1024) continue;
-    const int o = grad_ctas_per_sm(g, smem);
+    const int o = grad_ctas_per_sm(g, smem, grouped);
     if (o <= 0) continue;
     const double warps = (double)o * cta_threads(g) / 32.0;
     const double score = std::min(warps, 8.0) + (g == 16 || g == 32 ? 0.5 : 0.0);
@@ -91,8 +107,29 @@ lhaf_status grad_plan(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128*
   p.team_bytes = (int)tb;
   p.items_bytes = (int)ib;
   const int tpc = teams_per_cta(J.team);
-  uint64_t grid = (pl.T + tpc - 1) / tpc;
-  grid = std::min<uint64_t>(grid, (uint64_t)ctx->sms * (uint64_t)occ);
+  uint64_t chunks = (pl.T + tpc - 1) / tpc;
+  if (grouped) {
+    J.chunk_off.assign(1, 0);
+    for (const Plan& sub : subs) {
+      GradSieve g;
+      std::memset(&g, 0, sizeof(g));
+      fill_params(sub, false, false, J.team, flags & LHAF_PLAIN_ACCUM, g.p);
+      g.p.team_bytes = (int)tb;
+      g.p.items_bytes = (int)ib;
+      g.p.t_end = sub.T;
+      g.chat_off = (long long)J.pool;
+      J.pool += (size_t)sub.nd * sub.nd;
+      for (int q = 0; q < sub.P; q++) {  // pair q of the group is pair src_pair[q] of the full plan
+        g.smap[2 * q] = 2 * sub.src_pair[q];
+        g.smap[2 * q + 1] = 2 * sub.src_pair[q] + 1;
+      }
+      J.sv.push_back(g);
+      J.chunk_off.push_back(J.chunk_off.back() + (long long)((sub.T + tpc - 1) / tpc));
+    }
+    J.subs = std::move(subs);
+    chunks = (uint64_t)J.chunk_off.back();
+  }
+  uint64_t grid = std::min<uint64_t>(chunks, (uint64_t)ctx->sms * (uint64_t)occ);
   if (grid < 1) grid = 1;
   J.grid = grid;
   p.total_teams = grid * (uint64_t)tpc;
@@ -104,13 +141,32 @@ lhaf_status grad_plan(lhaf_ctx* ctx, int M, const lhaf_c128* B, const lhaf_c128*
   return LHAF_OK;
 }
 
+// Slot matrices of a job's sieves (its zero-digit groups, or the full plan) into chat (host).
+void grad_build_chats(const GradJob& J, int M, const lhaf_c128* B, const lhaf_c128* gamma, std::complex<double>* chat) {
+  if (J.sv.empty()) {
+    build_chat_host(J.pl, M, B, gamma, chat);
+    return;
+  }
+  for (size_t g = 0; g < J.subs.size(); g++) build_chat_host(J.subs[g], M, B, gamma, chat + J.sv[g].chat_off);
+}
+
+size_t grad_chat_entries(const GradJob& J) { return J.sv.empty() ? (size_t)J.pl.nd * J.pl.nd : J.pool; }
+
 // Adjoint launch, value reduction and gradient reduction of one item, ordered on the context's
 // stream: the slot matrix at chat, 6 doubles (dd value, value) at out6, the len gradient sums at
 // gout. The per-team gradient partials use ctx->b_gpart (reserved by the caller).
-lhaf_status grad_enqueue(lhaf_ctx* ctx, const GradJob& J, const double2* chat, double* out6, double2* gout) {
-  if (launch_grad(J.team, chat, J.p, (int)J.grid, ctx->d_partials, (double2*)ctx->b_gpart.p, ctx->stream) !=
-      cudaSuccess)
-    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "adjoint kernel");
+lhaf_status grad_enqueue(lhaf_ctx* ctx, const GradJob& J, const double2* chat, double* out6, double2* gout,
+                         const GradSieve* sv = nullptr, const long long* chunk_off = nullptr) {
+  if (J.sv.empty()) {
+    if (launch_grad(J.team, chat, J.p, (int)J.grid, ctx->d_partials, (double2*)ctx->b_gpart.p, ctx->stream) !=
+        cudaSuccess)
+      return (lhaf_status)record_cuda(cudaPeekAtLastError(), "adjoint kernel");
+  } else {
+    if (launch_grad_grouped(J.team, chat, sv, (int)J.sv.size(), chunk_off, J.chunk_off.back(), J.pl.nd - J.pl.bord,
+                            J.p.team_bytes, J.p.items_bytes, (int)J.grid, ctx->d_partials,
+                            (double2*)ctx->b_gpart.p, ctx->stream) != cudaSuccess)
+      return (lhaf_status)record_cuda(cudaPeekAtLastError(), "grouped adjoint kernel");
+  }
   if (launch_reduce(ctx->d_partials, (long long)J.p.total_teams, J.pl.h, out6, (double2*)(out6 + 4), ctx->stream) !=
       cudaSuccess)
     return (lhaf_status)record_cuda(cudaPeekAtLastError(), "value reduction");
@@ -170,14 +226,48 @@ extern "C" lhaf_status lhaf_grad(lhaf_ctx* ctx, int M, const lhaf_c128* B, const
     return LHAF_OK;
   }
   const int nd = J.pl.nd;
-  build_chat_host(J.pl, M, B, gamma, (std::complex<double>*)ctx->h_chat);
-  if (cudaMemcpyAsync(ctx->d_chat, ctx->h_chat, sizeof(double2) * nd * nd, cudaMemcpyHostToDevice, ctx->stream) !=
-      cudaSuccess)
-    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "slot matrix upload");
+  const double2* chat = ctx->d_chat;
+  const GradSieve* dsv = nullptr;
+  const long long* dco = nullptr;
+  if (J.sv.empty()) {
+    build_chat_host(J.pl, M, B, gamma, (std::complex<double>*)ctx->h_chat);
+    if (cudaMemcpyAsync(ctx->d_chat, ctx->h_chat, sizeof(double2) * nd * nd, cudaMemcpyHostToDevice, ctx->stream) !=
+        cudaSuccess)
+      return (lhaf_status)record_cuda(cudaPeekAtLastError(), "slot matrix upload");
+  } else {
+    // the zero-digit groups' slot matrices, descriptors and chunk offsets in the context's group buffers
+    BatchWork& w = ctx->gw;
+    const size_t ns = J.sv.size();
+    if (w.uploaded) {
+      if (const cudaError_t e = cudaEventSynchronize(w.uploaded); e != cudaSuccess)
+        return (lhaf_status)record_cuda(e, "cudaEventSynchronize");
+    } else if (cudaEventCreateWithFlags(&w.uploaded, cudaEventDisableTiming) != cudaSuccess) {
+      w.uploaded = nullptr;
+      return (lhaf_status)record_cuda(cudaPeekAtLastError(), "cudaEventCreate");
+    }
+    if (!w.h_chat.reserve(sizeof(double2) * J.pool) || !w.chat.reserve(sizeof(double2) * J.pool) ||
+        !w.h_items.reserve(sizeof(GradSieve) * ns) || !w.items.reserve(sizeof(GradSieve) * ns) ||
+        !w.h_chunks.reserve(sizeof(long long) * (ns + 1)) || !w.chunks.reserve(sizeof(long long) * (ns + 1)))
+      return LHAF_ENOMEM;
+    grad_build_chats(J, M, B, gamma, static_cast<std::complex<double>*>(w.h_chat.p));
+    std::memcpy(w.h_items.p, J.sv.data(), sizeof(GradSieve) * ns);
+    std::memcpy(w.h_chunks.p, J.chunk_off.data(), sizeof(long long) * (ns + 1));
+    if (cudaMemcpyAsync(w.chat.p, w.h_chat.p, sizeof(double2) * J.pool, cudaMemcpyHostToDevice, ctx->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(w.items.p, w.h_items.p, sizeof(GradSieve) * ns, cudaMemcpyHostToDevice, ctx->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(w.chunks.p, w.h_chunks.p, sizeof(long long) * (ns + 1), cudaMemcpyHostToDevice,
+                        ctx->stream) != cudaSuccess ||
+        cudaEventRecord(w.uploaded, ctx->stream) != cudaSuccess)
+      return (lhaf_status)record_cuda(cudaPeekAtLastError(), "group upload");
+    chat = static_cast<const double2*>(w.chat.p);
+    dsv = static_cast<const GradSieve*>(w.items.p);
+    dco = static_cast<const long long*>(w.chunks.p);
+  }
   if (!ctx->b_gpart.reserve(sizeof(double2) * (size_t)J.len * J.p.total_teams) ||
       !ctx->b_gout.reserve(sizeof(double2) * (size_t)J.len) || !ctx->hb_gout.reserve(sizeof(double2) * (size_t)J.len))
     return LHAF_ENOMEM;
-  st = grad_enqueue(ctx, J, ctx->d_chat, ctx->d_out, (double2*)ctx->b_gout.p);
+  st = grad_enqueue(ctx, J, chat, ctx->d_out, (double2*)ctx->b_gout.p, dsv, dco);
   if (st != LHAF_OK) return st;
   if (cudaMemcpyAsync(ctx->h_out, ctx->d_out, 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
       cudaMemcpyAsync(ctx->hb_gout.p, ctx->b_gout.p, sizeof(double2) * J.len, cudaMemcpyDeviceToHost, ctx->stream) !=
@@ -200,8 +290,8 @@ extern "C" lhaf_status lhaf_grad_batched(lhaf_ctx* ctx, int batch, int M, const 
   if (const cudaError_t e_ = (cudaSetDevice(ctx->device)); e_ != cudaSuccess) return (lhaf_status)record_cuda(e_, "cudaSetDevice");
   std::vector<GradJob> jobs(batch);
   std::vector<lhaf_status> ist(batch, LHAF_OK);
-  std::vector<size_t> chat_off(batch, 0), gout_off(batch, 0);
-  size_t pool = 0, gtot = 0, gpart = 1;
+  std::vector<size_t> chat_off(batch, 0), gout_off(batch, 0), sv_off(batch, 0), co_off(batch, 0);
+  size_t pool = 0, gtot = 0, gpart = 1, nsv = 0, nco = 0;
   for (int i = 0; i < batch; i++) {
     const lhaf_c128* gi = gammas ? gammas + (size_t)i * M : nullptr;
     const int32_t* ri = reps + (size_t)i * M;
@@ -209,7 +299,11 @@ extern "C" lhaf_status lhaf_grad_batched(lhaf_ctx* ctx, int batch, int M, const 
     if (ist[i] == LHAF_OK) ist[i] = grad_plan(ctx, M, B, gi, ri, flags, jobs[i]);
     if (ist[i] != LHAF_OK || jobs[i].pl.N == 0) continue;
     chat_off[i] = pool;
-    pool += (size_t)jobs[i].pl.nd * jobs[i].pl.nd;
+    pool += grad_chat_entries(jobs[i]);
+    sv_off[i] = nsv;
+    nsv += jobs[i].sv.size();
+    co_off[i] = nco;
+    nco += jobs[i].chunk_off.size();
     gout_off[i] = gtot;
     gtot += (size_t)jobs[i].len;
     gpart = std::max(gpart, (size_t)jobs[i].len * (size_t)jobs[i].p.total_teams);
@@ -222,19 +316,43 @@ extern "C" lhaf_status lhaf_grad_batched(lhaf_ctx* ctx, int batch, int M, const 
       !ctx->b_gout.reserve(sizeof(double2) * std::max<size_t>(gtot, 1)) ||
       !ctx->hb_gout.reserve(sizeof(double2) * std::max<size_t>(gtot, 1)))
     return LHAF_ENOMEM;
+  // the items' zero-digit group descriptors and chunk offsets (ctx->gw)
+  BatchWork& gw = ctx->gw;
+  if (nsv) {
+    if (gw.uploaded) {
+      if (const cudaError_t e = cudaEventSynchronize(gw.uploaded); e != cudaSuccess)
+        return (lhaf_status)record_cuda(e, "cudaEventSynchronize");
+    }
+    if (!gw.h_items.reserve(sizeof(GradSieve) * nsv) || !gw.items.reserve(sizeof(GradSieve) * nsv) ||
+        !gw.h_chunks.reserve(sizeof(long long) * nco) || !gw.chunks.reserve(sizeof(long long) * nco))
+      return LHAF_ENOMEM;
+  }
   if (w.uploaded) cudaEventSynchronize(w.uploaded);  // an earlier upload still reads the pinned buffer
   std::complex<double>* hc = static_cast<std::complex<double>*>(w.h_chat.p);
   for (int i = 0; i < batch; i++)
-    if (ist[i] == LHAF_OK && jobs[i].pl.N > 0)
-      build_chat_host(jobs[i].pl, M, B, gammas ? gammas + (size_t)i * M : nullptr, hc + chat_off[i]);
+    if (ist[i] == LHAF_OK && jobs[i].pl.N > 0) {
+      grad_build_chats(jobs[i], M, B, gammas ? gammas + (size_t)i * M : nullptr, hc + chat_off[i]);
+      if (!jobs[i].sv.empty()) {
+        std::memcpy(static_cast<GradSieve*>(gw.h_items.p) + sv_off[i], jobs[i].sv.data(),
+                    sizeof(GradSieve) * jobs[i].sv.size());
+        std::memcpy(static_cast<long long*>(gw.h_chunks.p) + co_off[i], jobs[i].chunk_off.data(),
+                    sizeof(long long) * jobs[i].chunk_off.size());
+      }
+    }
   if (pool && cudaMemcpyAsync(w.chat.p, hc, sizeof(double2) * pool, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
     return (lhaf_status)record_cuda(cudaPeekAtLastError(), "slot matrix upload");
+  if (nsv && (cudaMemcpyAsync(gw.items.p, gw.h_items.p, sizeof(GradSieve) * nsv, cudaMemcpyHostToDevice,
+                              ctx->stream) != cudaSuccess ||
+              cudaMemcpyAsync(gw.chunks.p, gw.h_chunks.p, sizeof(long long) * nco, cudaMemcpyHostToDevice,
+                              ctx->stream) != cudaSuccess))
+    return (lhaf_status)record_cuda(cudaPeekAtLastError(), "group upload");
   double* out = static_cast<double*>(w.out.p);
   double2* gout = static_cast<double2*>(ctx->b_gout.p);
   for (int i = 0; i < batch; i++) {
     if (ist[i] != LHAF_OK || jobs[i].pl.N == 0) continue;
     st = grad_enqueue(ctx, jobs[i], static_cast<const double2*>(w.chat.p) + chat_off[i], out + 6 * (size_t)i,
-                      gout + gout_off[i]);
+                      gout + gout_off[i], static_cast<const GradSieve*>(gw.items.p) + sv_off[i],
+                      static_cast<const long long*>(gw.chunks.p) + co_off[i]);
     if (st != LHAF_OK) return st;
   }
   if (cudaMemcpyAsync(w.h_out.p, w.out.p, sizeof(double) * 6 * (size_t)batch, cudaMemcpyDeviceToHost, ctx->stream) !=

@@ -152,10 +152,27 @@ cudaError_t launch_batch_gather(const double2* B, long long B_stride, const doub
                                 double2* chat_pool, float2* chat32_pool, cudaStream_t stream);
 
 // Adjoint: shared bytes per team, occupancy, the value+gradient kernel and the cross-team sum.
-size_t grad_team_bytes(int nd, int H, int h, int bord, int team);  // team: 8, 16 or 32 lanes
-int grad_ctas_per_sm(int team, size_t smem_bytes);
+size_t grad_team_bytes(int nd, int H, int h, int bord, int team);  // team: 8, 16, 32 or 64 lanes
+int grad_ctas_per_sm(int team, size_t smem_bytes, bool grouped = false);
 cudaError_t launch_grad(int team, const double2* chat, const TermParams& p, int grid, double* partials,
                         double2* gpart, cudaStream_t stream);
+
+// One sieve of the adjoint over zero-digit groups: its term parameters (t_end = its term count),
+// its slot matrix at chat_off in the pool, and the full problem's slot of each of its slots.
+struct GradSieve {
+  TermParams p;
+  long long chat_off;
+  int smap[kMaxDim];
+};
+static_assert(sizeof(GradSieve) % 8 == 0, "GradSieve is copied as 8-byte words");
+
+// The adjoint over several sieves in one launch: chunks of teams_per_cta(team) terms of one sieve
+// (sieve j owns chunks chunk_off[j] .. chunk_off[j+1]-1), CTA c taking chunks c, c + grid, ...;
+// each team keeps its gradient sums in the full problem's n_full slots (gpart slice
+// n_full^2 + n_full per team) and its dd value partial (4 doubles per team in partials).
+cudaError_t launch_grad_grouped(int team, const double2* chat_pool, const GradSieve* sieves, int n_sieves,
+                                const long long* chunk_off, long long n_chunks, int n_full, int team_bytes,
+                                int items_bytes, int grid, double* partials, double2* gpart, cudaStream_t stream);
 cudaError_t launch_grad_reduce(const double2* gpart, long long teams, int len, int h, double2* out,
                                cudaStream_t stream);
 

@@ -186,6 +186,7 @@ bool split_zero_digits(const Plan& pl, std::vector<Plan>& subs) {
     s.wscale = ws;
     for (int q = 0; q < pl.P; q++) {
       if (inZ[q]) continue;
+      s.src_pair.push_back(q);
       s.slot_mode.push_back(pl.slot_mode[2 * q]);
       s.slot_mode.push_back(pl.slot_mode[2 * q + 1]);
       s.eta.push_back(pl.eta[q]);

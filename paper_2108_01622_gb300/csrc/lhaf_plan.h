@@ -23,6 +23,7 @@ struct Plan {
   int M = 0, N = 0, h = 0, H = 0, Hl = 0, bord = 0, P = 0, nd = 0;
   int hp = 0, hp_even = 0;
   std::vector<int> slot_mode, eta, radix, skip;
+  std::vector<int> src_pair;  // a zero-digit group's pairs: their index in the plan it came from
   double wscale = 1.0;
   uint64_t T = 0;
 };

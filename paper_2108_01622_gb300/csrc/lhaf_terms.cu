@@ -256,7 +256,8 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
                                             unsigned char* smem, unsigned long long team_global,
                                             typename Cx<R>::t* __restrict__ stage, double* __restrict__ wstage,
                                             long long stage_ld, double* acc,
-                                            typename Cx<R>::t* __restrict__ gpart = nullptr) {
+                                            typename Cx<R>::t* __restrict__ gslice = nullptr,
+                                            const int* __restrict__ smap = nullptr, int n_full = 0) {
   using V = typename Cx<R>::t;
   constexpr int SG = G < 32 ? G : 32;  // lanes of the first warp of a team
 
@@ -283,20 +284,18 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
   // adjoint buffers (GRAD): S and Kb (nd x ld each), q_bar ((nd + 1) x (Hl + 1)), the region that
   // the adjoint's phases share (series adjoints, then c_bar, then multipliers, their adjoints and
   // dot-product partials: adjoint_union entries) and the pivot rows (nd ints) in shared memory; the
-  // gradient sums Ga (n x n) and Gv (n) in the team's own slice of gpart (global memory, which
-  // leaves shared memory for a fourth CTA on an SM at n = 27)
+  // gradient sums Ga (n x n) and Gv (n), or n_full x n_full and n_full through the slot map smap, in
+  // the team's own zeroed slice gslice of global memory (which leaves shared memory for a fourth
+  // CTA on an SM at n = 27)
   const int ng = nd - bord;
   V* gS = reinterpret_cast<V*>(reinterpret_cast<unsigned char*>(ts) + ((sizeof(TeamScratch) + 15) & ~(size_t)15));
   V* gK = gS + nd * ld;
   V* gQ = gK + nd * ld;
   V* gU = gQ + (nd + 1) * (Hl + 1);
   int* gpiv = reinterpret_cast<int*>(gU + adjoint_union(nd, H, Hl, G));
-  V* gA = GRAD ? gpart + (size_t)team_global * (size_t)(ng * ng + ng) : nullptr;
-  V* gV = GRAD ? gA + ng * ng : nullptr;
-  if constexpr (GRAD) {
-    for (int w = lt; w < ng * ng + ng; w += G) gA[w] = zero;  // gV follows gA
-    team_sync<G>();
-  }
+  const int gn = smap ? n_full : ng;
+  V* gA = GRAD ? gslice : nullptr;
+  V* gV = GRAD ? gA + gn * gn : nullptr;
 
   for (unsigned long long rnd = 0; rnd < p.rounds; rnd++) {
     const unsigned long long t_raw = p.t_begin + team_global + rnd * p.total_teams;
@@ -951,7 +950,7 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
       if constexpr (GRAD) {
         adjoint_series_labudde<R, G>(W, gS, gK, gQ, gU, Sa, Sc, SR, Sp, Sz, Se, nd, ld, bord, h, H, Hl, lt);
         adjoint_elimination<R, G>(gS, gK, gU, gpiv, nd, ld, lt);
-        adjoint_accumulate<R, G>(gK, nd, ld, bord, ts->delta, ts->weight, gA, gV, lt);
+        adjoint_accumulate<R, G>(gK, nd, ld, bord, ts->delta, ts->weight, gA, gV, smap, gn, lt);
       }
     }
   }
@@ -1162,14 +1161,99 @@ grad_kernel(const double2* __restrict__ chat, const __grid_constant__ TermParams
   const int team = threadIdx.x / G;
   const int lt = threadIdx.x - team * G;
   const unsigned long long team_global = (unsigned long long)blockIdx.x * TEAMS + team;
+  const int ng = p.nd - p.bord;
+  double2* gslice = gpart + team_global * (unsigned long long)(ng * ng + ng);
+  for (int w = lt; w < ng * ng + ng; w += G) gslice[w] = make_double2(0.0, 0.0);
+  team_sync<G>();
   double acc[4];
-  sieve_terms<double, G, false, true>(chat, p, smem, team_global, nullptr, nullptr, 0, acc, gpart);
+  sieve_terms<double, G, false, true>(chat, p, smem, team_global, nullptr, nullptr, 0, acc, gslice);
   if (lt == 0) {
     double* o = partials + 4ull * team_global;
     o[0] = acc[0];
     o[1] = acc[1];
     o[2] = acc[2];
     o[3] = acc[3];
+  }
+}
+
+// Value and adjoint over several sieves (a loop hafnian's zero-digit groups) in one launch: CTA c
+// takes chunks c, c + grid, ... of TEAMS terms of one sieve each (a fixed assignment, so that the
+// FP64 gradient sums of a team always add the same terms in the same order), the smaller groups'
+// terms on their smaller matrices; each team's gradient sums stay in the full problem's slots
+// (n_full) through each sieve's slot map, and its double-double value partial covers its chunks.
+template <int G>
+__global__ void __launch_bounds__(cta_of(G))
+grad_grouped_kernel(const double2* __restrict__ chat_pool, const GradSieve* __restrict__ sieves, int n_sieves,
+                    const long long* __restrict__ chunk_off, long long n_chunks, int n_full, int team_bytes,
+                    int items_bytes, double* __restrict__ partials, double2* __restrict__ gpart) {
+  constexpr int CTA = cta_of(G);
+  constexpr int TEAMS = CTA / G;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ TermParams sp;
+  __shared__ int s_job, s_Hl;
+  const int team = threadIdx.x / G;
+  const int lt = threadIdx.x - team * G;
+  const unsigned long long team_global = (unsigned long long)blockIdx.x * TEAMS + team;
+  double2* gslice = gpart + team_global * (unsigned long long)(n_full * n_full + n_full);
+  for (int w = lt; w < n_full * n_full + n_full; w += G) gslice[w] = make_double2(0.0, 0.0);
+  if (threadIdx.x == 0) {
+    s_job = -1;
+    s_Hl = -1;
+  }
+  double rh = 0.0, rl = 0.0, ih = 0.0, il = 0.0;
+  for (long long k = blockIdx.x; k < n_chunks; k += gridDim.x) {
+    __syncthreads();  // the previous chunk no longer reads sp and the tables
+    int lo = 0, hi = n_sieves - 1;  // sieve of chunk k: the last j with chunk_off[j] <= k
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (chunk_off[mid] <= k) {
+        lo = mid;
+      } else {
+        hi = mid - 1;
+      }
+    }
+    const int j = lo;
+    if (j != s_job) {
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&sieves[j].p);
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sp);
+      for (int w = threadIdx.x; w < (int)(sizeof(TermParams) / 8); w += CTA) dst[w] = src[w];
+    }
+    __syncthreads();
+    const bool valid_desc = sp.nd >= 2 && sp.nd <= kMaxDim && sp.P <= kMaxPairs && sp.h <= kMaxDegree &&
+                            sp.Hl <= sp.nd && sp.n_items == sp.Hl * (sp.Hl - 1) / 2 &&
+                            sp.nd - sp.bord <= n_full;
+    if (!valid_desc) continue;  // a description outside the compiled limits adds nothing
+    if (j != s_job || sp.Hl != s_Hl) {
+      build_cta_tables<double, CTA>(sp, smem);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const unsigned long long t0 = (unsigned long long)(k - chunk_off[j]) * TEAMS;
+      const unsigned long long T = sieves[j].p.t_end;
+      const unsigned long long te = T < t0 + TEAMS ? T : t0 + TEAMS;
+      sp.t_begin = t0;
+      sp.t_end = te > t0 ? te : t0;
+      sp.t_lo = 0ull;
+      sp.rounds = 1;
+      sp.total_teams = TEAMS;
+      sp.team_bytes = team_bytes;
+      sp.items_bytes = items_bytes;
+      s_job = j;
+      s_Hl = sp.Hl;
+    }
+    __syncthreads();
+    double acc[4];
+    sieve_terms<double, G, false, true>(chat_pool + sieves[j].chat_off, sp, smem, (unsigned long long)team, nullptr,
+                                        nullptr, 0, acc, gslice, sieves[j].smap, n_full);
+    dd_add_dd(rh, rl, acc[0], acc[1]);
+    dd_add_dd(ih, il, acc[2], acc[3]);
+  }
+  if (lt == 0) {
+    double* o = partials + 4ull * team_global;
+    o[0] = rh;
+    o[1] = rl;
+    o[2] = ih;
+    o[3] = il;
   }
 }
 
@@ -1861,8 +1945,20 @@ static const void* pick_grad(int team) {
   return nullptr;
 }
 
-int grad_ctas_per_sm(int team, size_t smem_bytes) {
-  const void* k = pick_grad(team);
+template <int G> static const void* ggptr() { return (const void*)grad_grouped_kernel<G>; }
+
+static const void* pick_grad_grouped(int team) {
+  switch (team) {
+    case 8: return ggptr<8>();
+    case 16: return ggptr<16>();
+    case 32: return ggptr<32>();
+    case 64: return ggptr<64>();
+  }
+  return nullptr;
+}
+
+int grad_ctas_per_sm(int team, size_t smem_bytes, bool grouped) {
+  const void* k = grouped ? pick_grad_grouped(team) : pick_grad(team);
   if (!k) return 0;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -1884,6 +1980,19 @@ cudaError_t launch_grad(int team, const double2* chat, const TermParams& p, int 
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&chat, (void*)&p, (void*)&partials, (void*)&gpart};
+  return cudaLaunchKernel(k, dim3(grid), dim3(cta_of(team)), args, smem, stream);
+}
+
+cudaError_t launch_grad_grouped(int team, const double2* chat_pool, const GradSieve* sieves, int n_sieves,
+                                const long long* chunk_off, long long n_chunks, int n_full, int team_bytes,
+                                int items_bytes, int grid, double* partials, double2* gpart, cudaStream_t stream) {
+  const void* k = pick_grad_grouped(team);
+  if (!k || n_sieves <= 0 || n_full <= 0 || n_full > kMaxDim) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)items_bytes + (size_t)teams_per_cta(team) * team_bytes;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&chat_pool, (void*)&sieves, (void*)&n_sieves, (void*)&chunk_off, (void*)&n_chunks,
+                  (void*)&n_full, (void*)&team_bytes, (void*)&items_bytes, (void*)&partials, (void*)&gpart};
   return cudaLaunchKernel(k, dim3(grid), dim3(cta_of(team)), args, smem, stream);
 }
 

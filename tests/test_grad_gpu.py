@@ -131,6 +131,48 @@ def test_grad_37_wide_against_c_oracle_minors(ctx):
         assert abs(dg[m] - ref) <= 1e-9 * abs(ref)
 
 
+@pytest.mark.parametrize("team", [0, 8, 16, 64])
+def test_grad_zero_digit_groups_match_full_matrix(ctx, team, monkeypatch):
+    # patterns with even pairs: the adjoint over the zero-digit groups (each on its smaller matrix,
+    # gradient sums in the full problem's slots) equals the full-matrix sieve (LHAF_NO_ZERO_SPLIT)
+    # and the oracle's minors
+    import paper_2108_01622_gb300 as lg
+
+    if team:
+        monkeypatch.setenv("LHAF_GRAD_TEAM", str(team))
+    for reps, loops in (((2, 2, 1, 3), True), ((4, 2, 2), True), ((2, 2, 2, 2), False), ((2, 1, 2, 1, 2), True)):
+        p = wl.small_problem(seed=31 + sum(reps), M=len(reps), reps=reps, loops=loops)
+        assert lg.plan_groups(p.reps) >= 2
+        v1, dB1, dg1 = ctx.lhaf_grad(p.B, p.gamma, p.reps)
+        v2, dB2, dg2 = ctx.lhaf_grad(p.B, p.gamma, p.reps, flags=lg.NO_ZERO_SPLIT)
+        dB_ref, dg_ref = lo.lhaf_grad_minor(p.B, p.gamma, p.reps)
+        scale = max(np.abs(dB_ref).max(), np.abs(dg_ref).max(), abs(v2))
+        assert abs(v1 - v2) <= 1e-12 * scale
+        assert np.abs(dB1 - dB2).max() <= 1e-12 * scale and np.abs(dg1 - dg2).max() <= 1e-12 * scale
+        assert np.abs(dB1 - dB_ref).max() <= 1e-10 * scale and np.abs(dg1 - dg_ref).max() <= 1e-10 * scale
+
+
+def test_grad_batched_groups_match_single_calls(ctx):
+    # a batch mixing grouped and ungrouped outcomes of the 32-photon workload: per item the same
+    # bits as the single call (a fixed chunk assignment); against the full-matrix sieve, two FP64
+    # evaluations of one cancelling sum, within its condition number (C oracle) x 2^-52 x 32
+    import paper_2108_01622_gb300 as lg
+
+    b = wl.gradient_batch(seed=4, count=6)
+    R = np.stack(b.reps).astype(np.int32)
+    G = np.stack(b.gammas)
+    vals, dB, dg, st = ctx.lhaf_grad_batched(b.B, G, R)
+    assert np.all(st == 0)
+    for i in range(len(R)):
+        v, d1, g1 = ctx.lhaf_grad(b.B, G[i], R[i])
+        v2, d2, g2 = ctx.lhaf_grad(b.B, G[i], R[i], flags=lg.NO_ZERO_SPLIT)
+        s = max(np.abs(d2).max(), np.abs(g2).max())
+        assert vals[i] == v and np.array_equal(dB[i], d1) and np.array_equal(dg[i], g1)
+        _, cond = csieve.lhaf_with_condition(b.B, G[i], R[i], extended=False)
+        tol = max(1e-11, 32 * cond * 2.0 ** -52)
+        assert abs(v - v2) <= tol * abs(v2) and np.abs(d1 - d2).max() <= tol * s
+
+
 def test_log_prob_chain_rule_squeezing_displacement_phases(ctx):
     import torch
 
