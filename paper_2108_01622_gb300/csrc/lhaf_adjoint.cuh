@@ -41,6 +41,18 @@ __host__ __device__ constexpr int adjoint_union(int nd, int H, int Hl, int G) {
                                 : (6 * (H + 2) > 2 * nd + dots_slots(G) ? 6 * (H + 2) : 2 * nd + dots_slots(G)));
 }
 
+// 1/k for k <= kMaxDegree + 1, rounded once at compile time (the reverse series' step divisions
+// become multiplications: an FP64 division is a sequence of several FP64 instructions)
+struct InvTable {
+  double v[kMaxDegree + 2];
+};
+__host__ __device__ constexpr InvTable make_inv_table() {
+  InvTable t{};
+  for (int k = 1; k < kMaxDegree + 2; k++) t.v[k] = 1.0 / (double)k;
+  return t;
+}
+__constant__ InvTable c_inv = make_inv_table();
+
 template <typename V>
 __device__ __forceinline__ V q_fwd(const V* W, int ld, int nd, int l, int m) {
   // forward q_l[m] as La Budde left it: q_l[0] = 1, q_l[m] at W[l + m - 1][l] (1 <= m <= nd - l)
@@ -123,9 +135,10 @@ __device__ __forceinline__ void adjoint_series_labudde(const typename Cx<R>::t* 
   team_sync<G>();
   // e_m = (1/m) sum_(j=1..m) z_j e_(m-j), m = h .. 1
   for (int m = h; m >= 1; m--) {
-    const V em = eb[m];
-    const V t = cmake<V>(em.x / (R)m, em.y / (R)m);
-    for (int j = 1 + lt; j <= m; j += G) {
+    for (int j = 1 + lt; j <= m; j += G) {  // only the lanes with work form e_bar_m / m
+      const V em = eb[m];
+      const R im = (R)c_inv.v[m];
+      const V t = cmake<V>(em.x * im, em.y * im);
       cmac(zb[j], t, Se[m - j]);
       V e2 = eb[m - j];
       cmac(e2, t, Sz[j]);
@@ -282,7 +295,7 @@ __device__ __forceinline__ void adjoint_series_labudde(const typename Cx<R>::t* 
 // the subdiagonal (entries below the subdiagonal are zero in the state itself), piv the pivot
 // rows. On return S is the input matrix K (up to rounding) and Kb its adjoint. U holds the step's
 // multipliers l (U[0 .. nd)), their adjoints l_bar (U[nd .. 2 nd), with -sum l_bar l at index
-// k + 1) and the partial sums of team_dots.
+// k + 1 and 1 / p at index k) and the partial sums of team_dots.
 template <typename R, int G>
 __device__ __forceinline__ void adjoint_elimination(typename Cx<R>::t* S, typename Cx<R>::t* Kb,
                                                     typename Cx<R>::t* U, const int* piv, int nd, int ld, int lt) {
@@ -330,7 +343,10 @@ __device__ __forceinline__ void adjoint_elimination(typename Cx<R>::t* S, typena
         sl.y += part[w].y;
       }
     }
-    if (lt == 0) Lb[k1] = cmake<V>(flip(sl.x), flip(sl.y));
+    if (lt == 0) {  // -sum l_bar l and, in the free slot k, 1 / p for the multiplier adjoints
+      Lb[k1] = cmake<V>(flip(sl.x), flip(sl.y));
+      Lb[k] = crecip(p);
+    }
     team_sync<G>();
     // A = L^-1 K' on rows a >= k+2: A[a][k] = l_a p, A[a][j] = K'[a][j] + l_a K'[k1][j] (j >= k1);
     // item (a, column), column k first
@@ -361,7 +377,7 @@ __device__ __forceinline__ void adjoint_elimination(typename Cx<R>::t* S, typena
     // A_bar = (L^T Kb') L^-T on columns a >= k+2 (Kb[i][a] += Kb[i][k1] l_a), then the multiplier
     // adjoints Kb[a][k] += l_bar_a / p (a >= k+2) and Kb[k1][k] -= (sum_a l_bar_a l_a) / p: one
     // flat list of multiply-adds
-    const V ip = crecip(p);
+    const V ip = Lb[k];
     const int n3 = nd * m;
     for (int w = lt; w < n3 + m + 1; w += G) {
       const bool cl = w < n3;
