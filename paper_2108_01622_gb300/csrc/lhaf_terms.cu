@@ -900,24 +900,51 @@ __device__ __forceinline__ void sieve_terms(const typename Cx<R>::t* __restrict_
         __syncwarp();
         // Step k: R_{k+1}, p_k, z_k = (p_k + k R_{k+1}) / 2 and e_{k-1} = sum_j z_j e_{k-1-j}/(k-1)
         // from one reduction round (e lags one step, so its dot product needs no z_k).
+        // With 16 or more lanes the three dot products run side by side on three groups of SG / 4
+        // lanes (the fourth idle), each with a short shuffle tree: the trees' FP64 adds, not the
+        // products, dominate a step of a degree <= 32 series.
+        constexpr int GW = SG >= 16 ? SG / 4 : SG;
+        const int grp = sl / GW, gl = sl - grp * GW;
         for (int k = 1; k <= h + 1; k++) {
           const bool rp = k <= h;
           V sR = zero, sp = zero, se = zero;
-          for (int i = 1 + sl; i <= k; i += SG) {
-            if (rp) cmac(sR, Sa[i], SR[k + 1 - i]);
-            if (i < k) {
-              if (rp) cmac(sp, Sa[i], Sp[k - i]);
-              cmac(se, Sz[i], Se[k - 1 - i]);
+          if constexpr (SG >= 16) {
+            // group 0: sum_(i<=k) a_i R_(k+1-i); group 1: sum_(i<k) a_i p_(k-i); group 2: sum_(i<k) z_i e_(k-1-i)
+            const int top = grp == 0 ? k : k - 1;
+            const bool on = grp < 3 && (grp == 2 || rp);
+            V sg = zero;
+            for (int i = 1 + gl; i <= k; i += GW) {
+              const bool v = on && i <= top;
+              const int iy = v ? (grp == 0 ? k + 1 - i : (grp == 1 ? k - i : k - 1 - i)) : 0;
+              const V x = grp == 2 ? Sz[i] : Sa[i];
+              const V y = grp == 0 ? SR[iy] : (grp == 1 ? Sp[iy] : Se[iy]);
+              cmac(sg, v ? x : zero, y);
             }
-          }
 #pragma unroll
-          for (int off = SG / 2; off >= 1; off >>= 1) {
-            sR.x += __shfl_xor_sync(0xffffffffu, sR.x, off);
-            sR.y += __shfl_xor_sync(0xffffffffu, sR.y, off);
-            sp.x += __shfl_xor_sync(0xffffffffu, sp.x, off);
-            sp.y += __shfl_xor_sync(0xffffffffu, sp.y, off);
-            se.x += __shfl_xor_sync(0xffffffffu, se.x, off);
-            se.y += __shfl_xor_sync(0xffffffffu, se.y, off);
+            for (int off = GW / 2; off >= 1; off >>= 1) {
+              sg.x += __shfl_xor_sync(0xffffffffu, sg.x, off);
+              sg.y += __shfl_xor_sync(0xffffffffu, sg.y, off);
+            }
+            sR = cmake<V>(__shfl_sync(0xffffffffu, sg.x, 0, SG), __shfl_sync(0xffffffffu, sg.y, 0, SG));
+            sp = cmake<V>(__shfl_sync(0xffffffffu, sg.x, GW, SG), __shfl_sync(0xffffffffu, sg.y, GW, SG));
+            se = cmake<V>(__shfl_sync(0xffffffffu, sg.x, 2 * GW, SG), __shfl_sync(0xffffffffu, sg.y, 2 * GW, SG));
+          } else {
+            for (int i = 1 + sl; i <= k; i += SG) {
+              if (rp) cmac(sR, Sa[i], SR[k + 1 - i]);
+              if (i < k) {
+                if (rp) cmac(sp, Sa[i], Sp[k - i]);
+                cmac(se, Sz[i], Se[k - 1 - i]);
+              }
+            }
+#pragma unroll
+            for (int off = SG / 2; off >= 1; off >>= 1) {
+              sR.x += __shfl_xor_sync(0xffffffffu, sR.x, off);
+              sR.y += __shfl_xor_sync(0xffffffffu, sR.y, off);
+              sp.x += __shfl_xor_sync(0xffffffffu, sp.x, off);
+              sp.y += __shfl_xor_sync(0xffffffffu, sp.y, off);
+              se.x += __shfl_xor_sync(0xffffffffu, se.x, off);
+              se.y += __shfl_xor_sync(0xffffffffu, se.y, off);
+            }
           }
           if (sl == 0) {
             if (rp) {
