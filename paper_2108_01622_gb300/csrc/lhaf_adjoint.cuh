@@ -328,19 +328,26 @@ __device__ __forceinline__ void adjoint_elimination(typename Cx<R>::t* S, typena
           Lb[a] = s;
           cmac(sl, s, la);
         });
+    // lane 0 needs the sum; with two warps and at most 32 outputs (lanes 0 .. m-1) the second
+    // warp holds nothing and skips its tree (the condition is uniform over the team)
+    const bool one_warp = G > 32 && m <= 32;
+    if (G <= 32 || lt < 32 || !one_warp) {
 #pragma unroll
-    for (int off = SG / 2; off >= 1; off >>= 1) {
-      sl.x += __shfl_xor_sync(0xffffffffu, sl.x, off);
-      sl.y += __shfl_xor_sync(0xffffffffu, sl.y, off);
+      for (int off = SG / 2; off >= 1; off >>= 1) {
+        sl.x += __shfl_xor_sync(0xffffffffu, sl.x, off);
+        sl.y += __shfl_xor_sync(0xffffffffu, sl.y, off);
+      }
     }
     if constexpr (G > 32) {  // two warps: their sums meet in the (now free) partials
-      team_sync<G>();
-      if ((lt & 31) == 0) part[lt >> 5] = sl;
-      team_sync<G>();
-      sl = part[0];
-      for (int w = 1; w < G / 32; w++) {
-        sl.x += part[w].x;
-        sl.y += part[w].y;
+      if (!one_warp) {
+        team_sync<G>();
+        if ((lt & 31) == 0) part[lt >> 5] = sl;
+        team_sync<G>();
+        sl = part[0];
+        for (int w = 1; w < G / 32; w++) {
+          sl.x += part[w].x;
+          sl.y += part[w].y;
+        }
       }
     }
     if (lt == 0) {  // -sum l_bar l and, in the free slot k, 1 / p for the multiplier adjoints
