@@ -56,8 +56,8 @@ PEAK_SOURCE = "derived: 152 SMs x 4 sub-partitions x 0.5 FP64 FMA lanes/clk x 2 
 # full-size launch, valid only for the kernel source it was taken on (else reported as null)
 KERNEL_TRAFFIC = {
     # workload: (sha256[:16] of csrc/lhaf_terms.cu at capture, bytes of the captured launch, its terms)
-    "large60": ("90601fc1cdf465c3", 626944 + 57232128, 110557),
-    "collision40": ("90601fc1cdf465c3", 221952 + 0, 34560),
+    "large60": ("ac3da7541ec2bfa6", 437760 + 57118208, 110557),
+    "collision40": ("ac3da7541ec2bfa6", 223488 + 0, 34560),
 }
 
 
