@@ -152,6 +152,23 @@ def test_grad_zero_digit_groups_match_full_matrix(ctx, team, monkeypatch):
         assert np.abs(dB1 - dB_ref).max() <= 1e-10 * scale and np.abs(dg1 - dg_ref).max() <= 1e-10 * scale
 
 
+def test_grad_too_many_groups_runs_the_full_matrix(ctx):
+    # 26 modes with two photons each: 13 pairs of count 2, 2^13 - 1 zero-digit groups, above the
+    # grouped adjoint's 4096, so the full-matrix adjoint runs (the same bits as LHAF_NO_ZERO_SPLIT);
+    # the value against the C oracle
+    import paper_2108_01622_gb300 as lg
+
+    b = wl.gradient_batch(seed=12, count=1, n_photons=2)
+    reps = np.zeros(40, np.int32)
+    reps[np.random.default_rng(12).choice(40, 26, replace=False)] = 2
+    assert lg.plan_groups(reps) > 4096
+    v1, dB1, dg1 = ctx.lhaf_grad(b.B, b.gammas[0], reps)
+    v2, dB2, dg2 = ctx.lhaf_grad(b.B, b.gammas[0], reps, flags=lg.NO_ZERO_SPLIT)
+    assert v1 == v2 and np.array_equal(dB1, dB2) and np.array_equal(dg1, dg2)
+    ref, cond = csieve.lhaf_with_condition(b.B, b.gammas[0], reps, extended=False)
+    assert abs(v1 - ref) <= max(1e-10, 32 * cond * 2.0 ** -52) * abs(ref)
+
+
 def test_grad_batched_groups_match_single_calls(ctx):
     # a batch mixing grouped and ungrouped outcomes of the 32-photon workload: per item the same
     # bits as the single call (a fixed chunk assignment); against the full-matrix sieve, two FP64
