@@ -27,8 +27,9 @@ constexpr int kMaxGammaVectors = 256;
 // Below this many vectors a pattern with zero-digit groups runs as one batch of single loop
 // hafnians instead: the batch deletes the delta' = 0 slots group by group, which the shared
 // reduction here cannot, and on GB300 that is worth more than sharing the reduction among few
-// vectors (the 40-photon collision pattern: 4 vectors 0.94x, 16 vectors 1.03x, 64 vectors 1.13x
-// against the batch).
+// vectors (the 40-photon collision pattern: the shared reduction ran 4 vectors at 0.94x the batch;
+// from 16 vectors on it wins, 1.03x to 1.12x). The dispatch itself does no more host work than a
+// plan: the batch checks the values.
 constexpr int kMultiMinVectorsWithGroups = 16;
 
 }  // namespace
@@ -40,21 +41,16 @@ extern "C" lhaf_status lhaf_multi_gamma(lhaf_ctx* ctx, int M, const lhaf_c128* B
     return LHAF_EINVAL;
   if (flags & ~(uint32_t)(LHAF_PLAIN_ACCUM | LHAF_NO_REPEAT_SPEEDUP)) return LHAF_EINVAL;
   if (stats) std::memset(stats, 0, sizeof(*stats));
-  for (int a = 0; a < M; a++) {
+  for (int a = 0; a < M; a++)
     if (reps[a] < 0) return LHAF_EINVAL;
-    if (reps[a] == 0) continue;
-    for (int g = 0; g < n_gamma; g++)
-      if (!finite_c(gammas[(size_t)g * M + a])) return LHAF_EINVAL;
-    for (int b = 0; b < M; b++)
-      if (reps[b] > 0 && !finite_c(B[(size_t)std::min(a, b) * M + std::max(a, b)])) return LHAF_EINVAL;
-  }
   Plan pl;
   lhaf_status st = build_plan(M, reps, flags, true, pl);
   if (st != LHAF_OK) return st;
   if ((pl.N + 1) / 2 > kStageMaxDegree) return LHAF_ETOOBIG;  // the staged series limit (either path)
   if (pl.N > 0 && n_gamma < kMultiMinVectorsWithGroups) {
-    std::vector<Plan> subs;
-    if (split_zero_digits(pl, subs)) {  // few vectors on a pattern with zero-digit groups: batch them
+    int even = 0;  // zero-digit groups exist: split_zero_digits' condition, without building them
+    for (int q = 0; q < pl.P; q++) even += (pl.eta[q] >= 2 && pl.eta[q] % 2 == 0) ? 1 : 0;
+    if (even >= 1 && even <= 20) {  // few vectors on a pattern with zero-digit groups: batch them (it checks the values)
       std::vector<int32_t> rr((size_t)n_gamma * M);
       for (int g = 0; g < n_gamma; g++) std::memcpy(rr.data() + (size_t)g * M, reps, sizeof(int32_t) * M);
       std::vector<lhaf_status> ist(n_gamma);
@@ -64,6 +60,13 @@ extern "C" lhaf_status lhaf_multi_gamma(lhaf_ctx* ctx, int M, const lhaf_c128* B
         if (x != LHAF_OK) return x;
       return LHAF_OK;
     }
+  }
+  for (int a = 0; a < M; a++) {
+    if (reps[a] == 0) continue;
+    for (int g = 0; g < n_gamma; g++)
+      if (!finite_c(gammas[(size_t)g * M + a])) return LHAF_EINVAL;
+    for (int b = 0; b < M; b++)
+      if (reps[b] > 0 && !finite_c(B[(size_t)std::min(a, b) * M + std::max(a, b)])) return LHAF_EINVAL;
   }
   std::lock_guard<std::mutex> lock(ctx->mu);
   if (const cudaError_t e = cudaSetDevice(ctx->device); e != cudaSuccess)
